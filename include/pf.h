@@ -1,0 +1,198 @@
+/*
+ * pf.h -- C-ABI of the GB300 (sm_103a) implementation of the decoupled
+ * phase-field scheme for two immiscible dielectric fluids
+ * (Yang, Christov & Dong, arXiv 2305.09020).
+ *
+ * The library advances the per-time-step path of Algorithm 1 (2D, eqs. 54-59)
+ * and Algorithm 2 (3D hybrid Fourier/spectral element, eqs. 74-78):
+ *   potential V -> field E -> auxiliary psi -> phase field phi -> pressure P
+ *   -> velocity u, each a constant-coefficient Helmholtz problem per Fourier
+ * mode (Remark after Algorithm 2), solved by fast diagonalisation with 1D
+ * generalised eigenbases computed once at set-up.
+ *
+ * Conventions shared by every entry point
+ *  - Return 0 (PF_OK) on success, a negative PF_E* code on failure; the
+ *    handle's message is then readable with pf_last_error().
+ *  - Host buffers are always owned by the caller; the library never keeps a
+ *    pointer to them after the call returns.
+ *  - Device memory is owned by the handle (allocated in pf_create, freed in
+ *    pf_destroy); all work is issued on the stream given to pf_create.
+ *  - Field layout: values at the unique tensor-product GLL nodes, ordered
+ *    [z][y][x] with x fastest.  n_x = ex*order (x is periodic),
+ *    n_y = ey*order + 1, Nz planes in z (Nz = 1 for 2D).  Public values are
+ *    double precision whatever the internal precision.
+ *  - Boundaries: x (and z) periodic; y = yb[0] is the solid wall
+ *    (u = 0, wetting condition eq. 19 with contact angle theta_s), y = yb[ey]
+ *    is the open side (eqs. a19, a24: P = 0, du/dn = 0).  The potential takes
+ *    a whole-side Dirichlet (electrode) or homogeneous Neumann condition on
+ *    each of the two sides (eq. 21 with an electrode covering the side).
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define PF_OK             0
+#define PF_EINVAL        -1   /* invalid argument (sizes, pointers, parameters)            */
+#define PF_ENOMEM        -2   /* device or host allocation failed                          */
+#define PF_ECUDA         -3   /* a CUDA runtime call or kernel launch failed              */
+#define PF_ENOTSEPARABLE -4   /* boundary data that is not a whole-side condition         */
+#define PF_EDIVERGED     -5   /* a non-finite value appeared in the state                  */
+#define PF_ETIMEOUT      -6   /* a bounded device-side wait gave up                        */
+#define PF_ESTATE        -7   /* call not valid in the handle's current state              */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+#define PF_BC_DIRICHLET 0
+#define PF_BC_NEUMANN   1
+
+#define PF_FP64  0   /* every kernel in double precision                                  */
+#define PF_MIXED 1   /* node-wise kernels, FFT and eigenbasis GEMMs in single precision;  */
+                     /* set-up, the initial-potential fixed point and reductions in FP64  */
+
+/* boundary-condition sets of the Helmholtz solves (y-direction; x is periodic) */
+#define PF_BCSET_V   0   /* the potential: per-side Dirichlet/Neumann from pf_vbc           */
+#define PF_BCSET_NN  1   /* psi and phi: natural (Neumann) on both sides, eq. 56-57        */
+#define PF_BCSET_P   2   /* pressure: natural on the wall, Dirichlet on the open side, 58  */
+#define PF_BCSET_U   3   /* velocity: Dirichlet on the wall, natural on the open side, 59  */
+
+/* field selection mask for pf_get_fields / pf_set_fields, in this order */
+#define PF_FIELD_V    1u    /* potential V                                                 */
+#define PF_FIELD_E    2u    /* electric field Ex, Ey, Ez (3 blocks; Ez = 0 in 2D)         */
+#define PF_FIELD_PHI  4u    /* phase field phi                                             */
+#define PF_FIELD_PSI  8u    /* auxiliary psi of eq. 44 (get only)                         */
+#define PF_FIELD_P   16u    /* pressure P                                                  */
+#define PF_FIELD_U   32u    /* velocity ux, uy, uz (3 blocks; uz = 0 in 2D)               */
+#define PF_FIELD_OLD 64u    /* with PF_FIELD_V/PHI/P/U: the level n-1 copies (restart)   */
+
+/* ---- descriptors ----------------------------------------------------------------------- */
+typedef struct pf_handle pf_handle;   /* opaque; owns all device memory */
+
+typedef struct {
+    int ex, ey;            /* elements in x (periodic) and y                               */
+    const double *xb;      /* ex+1 increasing breakpoints in x (period xb[ex]-xb[0])       */
+    const double *yb;      /* ey+1 increasing breakpoints in y (graded meshes allowed)     */
+    int order;             /* element order K (K+1 GLL nodes per direction), 2 <= K <= 15  */
+    int nz;                /* Fourier planes in z: 1 (2D) or an even power of two <= 1024  */
+    double lz;             /* period in z (ignored when nz == 1)                           */
+} pf_mesh;
+
+typedef struct {
+    double rho1, rho2;     /* densities of fluid 1 (phi = +1) and fluid 2 (phi = -1)       */
+    double mu1, mu2;       /* dynamic viscosities                                          */
+    double eps1, eps2;     /* relative permittivities (mixture law eq. interpolation)     */
+    double sigma;          /* surface tension; lambda = 3 sigma eta / (2 sqrt 2)           */
+    double eta;            /* interface thickness (Cahn number)                            */
+    double gamma1;         /* mobility                                                     */
+    double theta_s_deg;    /* static contact angle on the wall, eq. theta_def (90 = none)  */
+} pf_fluid;
+
+typedef struct {
+    int bottom_kind, top_kind;   /* PF_BC_DIRICHLET (electrode) or PF_BC_NEUMANN (gap)     */
+    double v_bottom, v_top;      /* electrode voltages for Dirichlet sides                 */
+} pf_vbc;
+
+typedef struct {
+    double dt;          /* time step                                                       */
+    int bdf;            /* 1 or 2 (BDF order J of Sec. 3.1; J = 1 is used for step 1)      */
+    int precision;      /* PF_FP64 or PF_MIXED                                             */
+    double S;           /* stabiliser; 0 -> eta^2 sqrt(4 gamma0 / (lambda gamma1 dt))      */
+    double nu_m;        /* 0 -> max(mu1,mu2)/min(rho1,rho2)                                */
+    double rho0;        /* 0 -> min(rho1,rho2)                                             */
+    double eps0;        /* 0 -> max(eps1,eps2)                                             */
+} pf_scheme;
+
+/* ---- host-only set-up helpers (no GPU needed) ------------------------------------------ */
+
+/* GLL tables of order K (Sec. 3.2.1 element basis): nodes[K+1], weights[K+1] and the
+ * differentiation matrix D[(K+1)*(K+1)], D[i*(K+1)+j] = l_j'(x_i).  Returns PF_EINVAL
+ * for K < 1 or K > 31 or null pointers. */
+int pf_gll(int K, double *nodes, double *weights, double *D);
+
+/* GLL node coordinates of ne elements of order K with breakpoints br[ne+1] along one
+ * direction (the unique nodes of Sec. 3.2.1): n = ne*K values when periodic != 0 (the
+ * last node is the first one shifted by the period), else ne*K + 1. */
+int pf_nodes_1d(int ne, const double *br, int K, int periodic, double *nodes);
+
+/* Assembled 1D stiffness (dense n x n, row-major) and diagonal GLL mass (n) of
+ * ne elements of order K with breakpoints br[ne+1]; periodic != 0 identifies the
+ * last node with the first (n = ne*K), else n = ne*K + 1.  These are the 1D
+ * factors of the tensor-product operators of eqs. 54-59. */
+int pf_operators_1d(int ne, const double *br, int K, int periodic, double *Kmat, double *Mdiag);
+
+/* Generalised eigenbasis of the 1D operator restricted to the free nodes:
+ * Kmat s = lambda Mdiag s with s^T Mdiag s = 1 (fast-diagonalisation factor of the
+ * constant matrices of the Remark after Algorithm 2).  dirichlet[n] flags removed
+ * nodes.  Output S[n*n] row-major: column c is the c-th eigenvector (ascending
+ * lambda), rows of Dirichlet nodes are zero and the last (#Dirichlet) columns are
+ * zero padding with lam = 1.  Returns PF_EINVAL on bad sizes. */
+int pf_fdm_1d(int n, const double *Kmat, const double *Mdiag, const unsigned char *dirichlet,
+              double *S, double *lam);
+
+/* ---- handle life cycle ------------------------------------------------------------------ */
+
+/* Validate the descriptors, build the 1D tables and eigenbases (FP64), allocate
+ * the device state, set phi^0 (host, [z][y][x], required) and u^0 (host, three
+ * consecutive blocks ux,uy,uz, nullable -> 0), P^0 = 0, compute V^0 by the fixed
+ * point of the Remark in Sec. 3.1 (FP64 on the device) and E^0.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: PF_EINVAL (bad descriptor), PF_ENOMEM, PF_ECUDA. *out is NULL on error. */
+int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc,
+              const pf_scheme *scheme, const double *phi0, const double *u0,
+              void *cuda_stream, pf_handle **out);
+
+/* Advance nsteps time steps (Algorithm 1 / 2).  The first step of a run uses
+ * BDF1; later steps the scheme's order.  Asynchronous on the handle's stream
+ * except when it returns an error found on the host.  nsteps >= 0. */
+int pf_step(pf_handle *h, int nsteps);
+
+/* Synchronise the handle's stream and check the state for non-finite values:
+ * returns PF_EDIVERGED if any was found since creation. */
+int pf_sync(pf_handle *h);
+
+/* Copy fields to the host (synchronous).  mask: PF_FIELD_* bits; blocks of
+ * n_x*n_y*Nz doubles in the order V, Ex, Ey, Ez, phi, psi, P, ux, uy, uz for
+ * the bits set (PF_FIELD_OLD selects level n-1 of V, phi, P, u).  n = capacity of
+ * host_out in doubles; PF_EINVAL if too small. */
+int pf_get_fields(pf_handle *h, unsigned mask, double *host_out, size_t n);
+
+/* Overwrite fields from host data, same layout as pf_get_fields (restart or warm
+ * start).  Setting PHI without OLD also sets level n-1 of phi; after a set the
+ * next step restarts the BDF history only if reset_history != 0. */
+int pf_set_fields(pf_handle *h, unsigned mask, const double *host_in, size_t n, int reset_history);
+
+/* FP64 diagnostics (synchronous): out[0] = int phi (phase mass), out[1] = max|u|,
+ * out[2] = time t, out[3] = step count, out[4] = number of V^0 fixed-point
+ * iterations, out[5] = 1 if a non-finite value was seen, out[6..7] = 0. */
+int pf_diagnostics(pf_handle *h, double out[8]);
+
+/* One fast-diagonalisation solve on a user right-hand side (synchronous):
+ *   (K + (lambda + beta_k^2) M) x = M f,   beta_k = 2 pi mode / lz,
+ * with homogeneous Dirichlet values on the Dirichlet sides of bcset
+ * (PF_BCSET_*; for PF_BCSET_V the handle's potential sides).  rhs/out are host
+ * arrays of n_x*n_y doubles ([y][x]) for mode 0 (and always in 2D) and two such
+ * planes (real, imaginary) for 0 < mode <= Nz/2.  Runs in the handle's precision.
+ * Errors: PF_EINVAL for a bad bcset or mode. */
+int pf_solve_helmholtz(pf_handle *h, int bcset, int mode, double lambda,
+                       const double *rhs, double *out);
+
+/* Geometry queries: nodes_x[n_x], nodes_y[n_y] (either may be NULL), sizes in dims[4]
+ * = {n_x, n_y, Nz, number of real values per field}. */
+int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]);
+
+/* Release all device memory of the handle (NULL is a no-op). */
+void pf_destroy(pf_handle *h);
+
+/* Last error message of the handle, or of the last failed pf_create when h is NULL. */
+const char *pf_last_error(const pf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H */

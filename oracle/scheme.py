@@ -30,8 +30,10 @@ Readings of the paper taken here (each also listed in the design notes):
 * grad(mu/rho) is taken by the chain rule on phi^{n+1};
 * g1 and g3 enter as in (phia) and (phic) (the forms the weak forms use);
 * the initial pressure is P^0 = 0 unless the caller supplies one;
-* the initial-potential fixed point starts from V^(0) = 0 and stops when
-  max|V^(k+1) - V^(k)| <= 1e-13 max(1, max|V_D|) (cap 20000 iterations);
+* the initial-potential fixed point ("upon convergence") starts from V^(0) = 0
+  and runs to the FP64 stagnation point: it stops when max|V^(k+1) - V^(k)| <=
+  1e-15 vmax, or once the update is below 1e-11 vmax and no longer decreases
+  (vmax = max(1, max|V_D|)); cap 20000 iterations;
 * the stability parameter defaults to S = eta^2 sqrt(4 gamma0 / (lambda
   gamma1 dt)) with gamma0 of the run's BDF order; a discriminant below 1e-10
   in the formula for alpha is set to 0.
@@ -281,7 +283,7 @@ class Solver:
         return np.concatenate(parts, axis=1)
 
     # ---- setup ---------------------------------------------------------------------------
-    def set_initial(self, phi0: np.ndarray, u0=None, P0=None, tol: float = 1e-13, max_iter: int = 20000):
+    def set_initial(self, phi0: np.ndarray, u0=None, P0=None, tol: float = 1e-15, max_iter: int = 20000):
         """phi^0, u^0 (eq. a26/a27), P^0, and V^0 by the fixed point of the Remark in Sec. 3.1."""
         self.phi = np.array(phi0, dtype=np.float64).reshape(self.nz, self.mesh.n2)
         self.phi_old = self.phi.copy()
@@ -318,20 +320,25 @@ class Solver:
                                 None if vD is None else vD[k], scale=self.prm.eps0)
         return out
 
-    def initial_potential(self, phi0, tol=1e-13, max_iter=20000):
+    def initial_potential(self, phi0, tol=1e-15, max_iter=20000):
+        """Fixed point of the Remark in Sec. 3.1, run to the FP64 stagnation point:
+        stop when max|V^(k+1) - V^(k)| <= tol * vmax, or when the update has fallen below
+        1e-11 * vmax and no longer decreases (round-off floor), or after max_iter."""
         s = self._src(0.0)
         vD = self._vD(s)
         V = np.zeros((self.nz, self.mesh.n2))
         vmax = 1.0
         if vD is not None:
             vmax = max(1.0, float(np.max(np.abs(np.concatenate([s["V_bot"].ravel(), s["V_top"].ravel()])))))
+        prev = math.inf
         for it in range(1, max_iter + 1):
             rhs = self.potential_rhs(phi0, V, s["fV"])
             Vn = self.ifft(self.solve_potential(rhs, vD))
             diff = float(np.max(np.abs(Vn - V)))
             V = Vn
-            if diff <= tol * vmax:
+            if diff <= tol * vmax or (diff <= 1e-11 * vmax and diff >= prev):
                 break
+            prev = diff
         self.v_iters = it
         return V
 

@@ -1,0 +1,51 @@
+"""Compile the in-tree CUDA library ``libpf.so`` for sm_103a with nvcc (no cmake)."""
+from __future__ import annotations
+
+import os
+import subprocess
+import hashlib
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(PKG, "csrc")
+ROOT = os.path.dirname(PKG)
+LIB = os.path.join(PKG, "libpf.so")
+SOURCES = ["pf_api.cu", "pf_setup.cpp"]
+HEADERS = ["pf_kernels.cuh"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    for f in SOURCES + HEADERS:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "pf.h"), "rb") as fh:
+        h.update(fh.read())
+    h.update(ARCH.encode())
+    return h.hexdigest()
+
+
+def nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libpf.so next to this file unless an up-to-date copy exists."""
+    stamp = LIB + ".sha256"
+    dig = _digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == dig:
+                return LIB
+    tmp = LIB + ".tmp"
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+           "-Xcompiler", "-ffp-contract=off", "-shared", "-o", tmp,
+           *[os.path.join(CSRC, f) for f in SOURCES]]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(dig)
+    return LIB

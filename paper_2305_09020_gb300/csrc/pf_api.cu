@@ -1,0 +1,850 @@
+// C-ABI of the decoupled phase-field step (declarations and contracts in include/pf.h).
+//
+// One handle owns an Engine<T> (T = double for PF_FP64, float for PF_MIXED) that
+// holds every device array of the step: 1D tables, eigenbases, the two BDF history
+// levels of the state, element-local right-hand sides and mode-plane work arrays.
+// A step is the kernel sequence of Algorithm 1 / Algorithm 2:
+//   k_potential -> k_fwd -> FDM -> k_inv (V, Ez) -> k_efield (Ex, Ey)
+//   k_chem -> k_fwd (psi RHS, Q2 modes) -> FDM (psi) -> k_rhs_phi -> FDM (phi)
+//   k_inv (phi, dphi/dz, W, dW/dz, L) -> k_momentum -> k_fwd -> FDM (P) -> k_inv (P)
+//   k_ugradp -> k_fwd x d -> FDM (u, all components batched) -> k_inv x d
+// The new level is written over level n-1, then the two levels swap roles.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_kernels.cuh"
+
+using pf::cplx;
+
+namespace {
+
+std::string g_create_error;
+
+struct CudaError {
+    cudaError_t code;
+    std::string where;
+};
+
+#define PF_CU(call)                                                                  \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) throw CudaError{e_, std::string(#call)};              \
+    } while (0)
+
+struct HostSetup {
+    int ex, ey, K, p, nx, ny, nz;
+    double lz;
+    std::vector<double> xb, yb, xi, w, D, Dw, hx, hy;
+    std::vector<double> Kx, Mx, Ky, My;          // assembled 1D operators
+    std::vector<double> Sx, Lx;                  // periodic x eigenbasis
+    std::vector<double> Sy[4], Ly[4];            // y eigenbases per bcset
+    std::vector<double> X, Y;                    // node coordinates
+    std::vector<double> liftV;                   // K_y[:, D] * V_D (potential lifting)
+    int vrow0 = -1, vrow1 = -1;                  // Dirichlet rows of the potential
+    double v0 = 0, v1 = 0;
+    // physics
+    double rho1, rho2, mu1, mu2, eps1, eps2, sigma, eta, gamma1, theta;
+    double dt, S, nu_m, rho0, eps0, lam, cos_theta;
+    int bdf, precision;
+};
+
+double alpha_of(const HostSetup &s, int J) {
+    // alpha of eq. 44; a discriminant below 1e-10 is taken as 0
+    const double g0 = J == 1 ? 1.0 : 1.5;
+    double disc = 1.0 - 4.0 * g0 * std::pow(s.eta, 4.0) / (s.lam * s.gamma1 * s.dt * std::pow(s.S, 2.0));
+    if (disc < 1e-10) disc = 0.0;
+    return -s.S / (2.0 * std::pow(s.eta, 2.0)) * (1.0 + std::sqrt(disc));
+}
+
+template <typename T>
+T *dalloc(size_t n) {
+    T *p = nullptr;
+    PF_CU(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)));
+    return p;
+}
+
+template <typename T>
+T *dupload(const std::vector<double> &v, cudaStream_t st) {
+    std::vector<T> h(v.begin(), v.end());
+    T *d = dalloc<T>(h.size());
+    PF_CU(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    PF_CU(cudaStreamSynchronize(st));
+    return d;
+}
+
+template <typename T>
+struct Engine {
+    const HostSetup &hs;
+    cudaStream_t st;
+    int ex, ey, K, p, nx, ny, n2, nz;
+    long long N, NL;
+    bool d3;
+    std::vector<void *> allocs;
+    // tables
+    T *hx, *hy, *D, *Dw, *w, *Mx, *My;
+    T *Sx, *SxT, *Lx, *Sy[4], *SyT[4], *Ly[4];
+    T *liftV;
+    cplx<T> *tw;
+    T *shV, *shP, *shPsi[2], *shPhi[2], *shU[2], *shTmp;
+    // state: level slots [0], [1]; cur = slot of level n
+    T *V[2], *Ez[2], *phi[2], *dzphi[2], *P[2], *dzP[2], *u[3][2], *dzu[3][2];
+    T *Ex, *Ey, *W, *dzW, *Lf, *Q2;
+    T *LA, *LB, *LAU[3], *LBU[3], *faceU;
+    T *RHS, *OUT, *PSIH, *Q2H, *FACEH, *W1, *W2;
+    double *red;
+    int cur = 0;
+
+    template <typename U>
+    U *mk(size_t n) {
+        U *q = dalloc<U>(n);
+        allocs.push_back(q);
+        PF_CU(cudaMemsetAsync(q, 0, std::max<size_t>(n, 1) * sizeof(U), st));
+        return q;
+    }
+    T *up(const std::vector<double> &v) {
+        T *q = dupload<T>(v, st);
+        allocs.push_back(q);
+        return q;
+    }
+
+    Engine(const HostSetup &s, cudaStream_t stream) : hs(s), st(stream) {
+        ex = s.ex; ey = s.ey; K = s.K; p = s.p; nx = s.nx; ny = s.ny; nz = s.nz;
+        n2 = nx * ny;
+        N = (long long)n2 * nz;
+        NL = (long long)ex * ey * p * p * nz;
+        d3 = nz > 1;
+        hx = up(s.hx); hy = up(s.hy); D = up(s.D); Dw = up(s.Dw); w = up(s.w);
+        Mx = up(s.Mx); My = up(s.My);
+        std::vector<double> tmp;
+        Sx = up(s.Sx);
+        tmp.assign(s.Sx.size(), 0.0);
+        for (int i = 0; i < nx; ++i)
+            for (int j = 0; j < nx; ++j) tmp[(size_t)i * nx + j] = s.Sx[(size_t)j * nx + i];
+        SxT = up(tmp);
+        Lx = up(s.Lx);
+        for (int b = 0; b < 4; ++b) {
+            Sy[b] = up(s.Sy[b]);
+            tmp.assign(s.Sy[b].size(), 0.0);
+            for (int i = 0; i < ny; ++i)
+                for (int j = 0; j < ny; ++j) tmp[(size_t)i * ny + j] = s.Sy[b][(size_t)j * ny + i];
+            SyT[b] = up(tmp);
+            Ly[b] = up(s.Ly[b]);
+        }
+        liftV = up(s.liftV);
+        {
+            std::vector<cplx<T>> h(std::max(1, nz / 2));
+            for (int k = 0; k < nz / 2; ++k) {
+                const double ang = -2.0 * M_PI * k / nz;
+                h[k] = {(T)std::cos(ang), (T)std::sin(ang)};
+            }
+            tw = mk<cplx<T>>(h.size());
+            PF_CU(cudaMemcpyAsync(tw, h.data(), h.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+        }
+        // per-plane shifts c + beta_k^2 of every solve (3 blocks for the batched velocity)
+        auto shifts = [&](double c) {
+            std::vector<double> v(3 * nz);
+            for (int pl = 0; pl < 3 * nz; ++pl) {
+                const int pp = pl % nz;
+                int k = 0;
+                if (nz > 1) k = (pp == 0) ? 0 : (pp == 1 ? nz / 2 : pp / 2);
+                const double beta = nz > 1 ? 2.0 * M_PI * k / s.lz : 0.0;
+                v[pl] = c + beta * beta;
+            }
+            return up(v);
+        };
+        shV = shifts(0.0);
+        shP = shifts(0.0);
+        for (int J = 1; J <= 2; ++J) {
+            const double al = alpha_of(s, J);
+            const double g0 = J == 1 ? 1.0 : 1.5;
+            shPsi[J - 1] = shifts(al + s.S / std::pow(s.eta, 2.0));
+            shPhi[J - 1] = shifts(-al);
+            shU[J - 1] = shifts(g0 / (s.nu_m * s.dt));
+        }
+        shTmp = mk<T>(3 * nz);
+        for (int l = 0; l < 2; ++l) {
+            V[l] = mk<T>(N); phi[l] = mk<T>(N); P[l] = mk<T>(N);
+            for (int c = 0; c < 3; ++c) u[l == 0 ? c : c][l] = nullptr;
+            for (int c = 0; c < (d3 ? 3 : 2); ++c) u[c][l] = mk<T>(N);
+            if (d3) {
+                Ez[l] = mk<T>(N); dzphi[l] = mk<T>(N); dzP[l] = mk<T>(N);
+                for (int c = 0; c < 3; ++c) dzu[c][l] = mk<T>(N);
+            } else {
+                Ez[l] = dzphi[l] = dzP[l] = nullptr;
+                for (int c = 0; c < 3; ++c) dzu[c][l] = nullptr;
+            }
+        }
+        if (!d3) { u[2][0] = u[2][1] = nullptr; }
+        Ex = mk<T>(N); Ey = mk<T>(N); W = mk<T>(N); Lf = mk<T>(N); Q2 = mk<T>(N);
+        dzW = d3 ? mk<T>(N) : nullptr;
+        LA = mk<T>(NL);
+        LB = d3 ? mk<T>(NL) : nullptr;
+        for (int c = 0; c < 3; ++c) {
+            LAU[c] = (c < 2 || d3) ? mk<T>(NL) : nullptr;
+            LBU[c] = d3 ? mk<T>(NL) : nullptr;
+        }
+        faceU = mk<T>((size_t)ex * p * nz);
+        RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
+        PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
+        red = mk<double>(1024);
+        PF_CU(cudaStreamSynchronize(st));
+    }
+    ~Engine() {
+        for (void *q : allocs) cudaFree(q);
+    }
+
+    pf::Geo<T> geo() const {
+        pf::Geo<T> g;
+        g.ex = ex; g.ey = ey; g.K = K; g.p = p; g.nx = nx; g.ny = ny; g.n2 = n2; g.nz = nz;
+        g.hx = hx; g.hy = hy; g.D = D; g.Dw = Dw; g.w = w; g.Mx = Mx; g.My = My;
+        return g;
+    }
+    pf::Phys<T> phys(int J) const {
+        pf::Phys<T> q;
+        q.rho1 = (T)hs.rho1; q.rho2 = (T)hs.rho2; q.mu1 = (T)hs.mu1; q.mu2 = (T)hs.mu2;
+        q.eps1 = (T)hs.eps1; q.eps2 = (T)hs.eps2; q.lam = (T)hs.lam;
+        q.inv_eta2 = (T)(1.0 / std::pow(hs.eta, 2.0)); q.gamma1 = (T)hs.gamma1;
+        q.S_eta2 = (T)(hs.S / std::pow(hs.eta, 2.0)); q.eps0 = (T)hs.eps0; q.rho0 = (T)hs.rho0;
+        q.nu_m = (T)hs.nu_m; q.dt = (T)hs.dt; q.sigma = (T)hs.sigma; q.cos_theta = (T)hs.cos_theta;
+        q.alpha = (T)alpha_of(hs, J); q.gamma0 = (T)(J == 1 ? 1.0 : 1.5); q.J = J;
+        q.wetting = std::fabs(hs.cos_theta) > 1e-15 ? 1 : 0;
+        return q;
+    }
+
+    // ---- launch helpers -----------------------------------------------------------------
+    int elem_threads() const { return ((p * p + 31) / 32) * 32; }
+    size_t elem_smem(int nfields) const { return (size_t)(2 * p * p + 32 + nfields * p * p) * sizeof(T); }
+    dim3 elem_grid() const { return dim3(ex * ey, nz); }
+    int fwd_tp() const {
+        int tp = (int)(24576 / (sizeof(cplx<T>) * (nz + 1)));
+        if (tp > 64) tp = 64;
+        if (tp < 4) tp = 4;
+        return tp;
+    }
+    void check_launch() { PF_CU(cudaGetLastError()); }
+
+    void gemm(const T *A, const T *B, T *C, long long Mrows, int Ncol, int R, int store, const T *lamN,
+              const T *lamR, const T *cpl, int cpl_mod) {
+        pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod};
+        constexpr int BM = 64, BN = 64, BK = sizeof(T) == 8 ? 8 : 16;
+        dim3 grid((Ncol + BN - 1) / BN, (unsigned)((Mrows + BM - 1) / BM));
+        pf::k_gemm<T, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g);
+        check_launch();
+    }
+
+    // fast-diagonalisation solve of nplanes mode planes: out = S_y [ (S_y^T rhs S_x) / (L_y + L_x + c_p) ] S_x^T
+    void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes) {
+        const long long P = nplanes;
+        gemm(rhs, Sx, W1, P * ny, nx, ny, 1, nullptr, nullptr, nullptr, 1);
+        gemm(W1, Sy[bcset], W2, P * nx, ny, nx, 0, Ly[bcset], Lx, sh, nz);
+        gemm(W2, SyT[bcset], W1, P * nx, ny, nx, 1, nullptr, nullptr, nullptr, 1);
+        gemm(W1, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1);
+    }
+
+    void fwd(const T *X0, int x0l, const T *X1, int x1l, int mult, double scale, const T *lift, T *out,
+             T *out1) {
+        pf::FwdArgs<T> a;
+        a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
+        a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
+        a.tw = tw; a.tp = fwd_tp();
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        pf::k_fwd<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        check_launch();
+    }
+
+    void inv(const T *Y, T *out, T *dzout, int drow0, double v0, int drow1, double v1) {
+        pf::InvArgs<T> a{};
+        a.Y = Y; a.phi_variant = 0; a.drow0 = drow0; a.drow1 = drow1; a.v0 = (T)v0; a.v1 = (T)v1;
+        a.out = out; a.dzout = d3 ? dzout : nullptr; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
+        a.tw = tw; a.tp = fwd_tp();
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        check_launch();
+    }
+
+    void inv_phi(double alpha, T *phi_out, T *dzphi_out) {
+        pf::InvArgs<T> a{};
+        a.Y = OUT; a.psi = PSIH; a.Q2h = Q2H; a.Q2n = Q2; a.alpha = (T)alpha;
+        a.S_eta2 = (T)(hs.S / std::pow(hs.eta, 2.0)); a.phi_variant = 1; a.drow0 = a.drow1 = -1;
+        a.out = phi_out; a.dzout = d3 ? dzphi_out : nullptr; a.out2 = W; a.dzout2 = d3 ? dzW : nullptr;
+        a.out3 = Lf; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz); a.tw = tw;
+        a.tp = std::max(4, fwd_tp() / 2);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>);
+        pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        check_launch();
+    }
+
+    // ---- the potential sub-step (also used by the initial fixed point) ----------------------
+    void potential(int J, const T *phin, const T *phio, const T *Vn, const T *Vo, const T *Ezn, const T *Ezo,
+                   T *Vout, T *Ezout) {
+        auto G = geo();
+        auto q = phys(J);
+        pf::k_potential<T><<<elem_grid(), elem_threads(), elem_smem(3), st>>>(G, q, phin, phio, Vn, Vo, Ezn,
+                                                                            Ezo, LA, d3 ? LB : nullptr);
+        check_launch();
+        fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
+        fdm(RHS, OUT, PF_BCSET_V, shV, nz);
+        inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
+    }
+
+    void efield(const T *Vf) {
+        const long long tot = N;
+        pf::k_efield<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(geo(), Vf, Ex, Ey);
+        check_launch();
+    }
+
+    // ---- one time step -----------------------------------------------------------------------
+    void step(int J) {
+        const int n = cur, o = 1 - cur;
+        auto G = geo();
+        auto q = phys(J);
+        const double al = alpha_of(hs, J);
+        // V^{n+1}, E^{n+1}
+        potential(J, phi[n], phi[o], V[n], V[o], Ez[n], Ez[o], V[o], Ez[o]);
+        efield(V[o]);
+        // psi^{n+1}
+        pf::k_chem<T><<<elem_grid(), elem_threads(), elem_smem(4), st>>>(
+            G, q, phi[n], phi[o], dzphi[n], dzphi[o], u[0][n], u[0][o], u[1][n], u[1][o], u[2][n], u[2][o], Ex,
+            Ey, Ez[o], LA, Q2, q.wetting ? faceU : nullptr);
+        check_launch();
+        fwd(LA, 1, Q2, 0, 1, 1.0, nullptr, RHS, Q2H);
+        fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz);
+        // phi^{n+1}
+        const T *faceh = nullptr;
+        if (q.wetting) {
+            const int tp = fwd_tp();
+            const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + tp * (nz + 1)) * sizeof(cplx<T>);
+            pf::k_face_fft<T><<<(nx + tp - 1) / tp, 256, smem, st>>>(G, faceU, FACEH, tw, tp);
+            check_launch();
+            faceh = FACEH;
+        }
+        pf::k_rhs_phi<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G, PSIH, faceh, RHS);
+        check_launch();
+        fdm(RHS, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
+        inv_phi(al, phi[o], dzphi[o]);
+        // P^{n+1}
+        pf::MomIn<T> mi;
+        mi.phi = phi[o]; mi.dzphi = dzphi[o]; mi.W = W; mi.dzW = dzW; mi.L = Lf;
+        mi.Ex = Ex; mi.Ey = Ey; mi.Ez = Ez[o];
+        for (int c = 0; c < 3; ++c) {
+            mi.un[c] = u[c][n]; mi.uo[c] = u[c][o]; mi.dzun[c] = dzu[c][n]; mi.dzuo[c] = dzu[c][o];
+        }
+        mi.Pn = P[n]; mi.Po = P[o]; mi.dzPn = dzP[n]; mi.dzPo = dzP[o];
+        pf::MomOut<T> mo;
+        mo.AP = LA; mo.BP = d3 ? LB : nullptr;
+        for (int c = 0; c < 3; ++c) { mo.AU[c] = LAU[c]; mo.BU[c] = LBU[c]; }
+        pf::k_momentum<T><<<elem_grid(), elem_threads(), elem_smem(12), st>>>(G, q, mi, mo);
+        check_launch();
+        fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr);
+        fdm(RHS, OUT, PF_BCSET_P, shP, nz);
+        inv(OUT, P[o], dzP[o], -1, 0.0, -1, 0.0);
+        // u^{n+1}
+        pf::k_ugradp<T><<<elem_grid(), elem_threads(), elem_smem(1), st>>>(G, q, P[o], LAU[0], LAU[1],
+                                                                         d3 ? LBU[2] : nullptr);
+        check_launch();
+        const int dc = d3 ? 3 : 2;
+        for (int c = 0; c < dc; ++c) fwd(LAU[c], 1, d3 ? LBU[c] : nullptr, 1, 0, 1.0, nullptr, RHS + c * N, nullptr);
+        fdm(RHS, OUT, PF_BCSET_U, shU[J - 1], dc * nz);
+        for (int c = 0; c < dc; ++c) inv(OUT + c * N, u[c][o], dzu[c][o], -1, 0.0, -1, 0.0);
+        cur = o;
+    }
+
+    // ---- reductions (FP64 accumulation) -------------------------------------------------------
+    double reduce(const T *x, const T *y, int kind) {
+        const int blocks = 512;
+        pf::k_reduce<T><<<blocks, 256, 0, st>>>(x, y, Mx, My, nx, n2, N, kind, red);
+        check_launch();
+        std::vector<double> h(blocks);
+        PF_CU(cudaMemcpyAsync(h.data(), red, blocks * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PF_CU(cudaStreamSynchronize(st));
+        double acc = 0.0;
+        for (int i = 0; i < blocks; ++i) {
+            const double v = h[i];
+            if (kind == 0) acc += v;
+            else if (v != v) return v;
+            else acc = std::max(acc, v);
+        }
+        return acc;
+    }
+};
+
+}  // namespace
+
+struct pf_handle {
+    HostSetup hs;
+    cudaStream_t st = nullptr;
+    std::unique_ptr<Engine<double>> e64;
+    std::unique_ptr<Engine<float>> e32;
+    long long nstep = 0;
+    double t = 0.0;
+    int v_iters = 0;
+    int last_J = 1;
+    bool diverged = false;
+    std::string err;
+};
+
+namespace {
+
+int fail(pf_handle *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(pf_handle *h, const CudaError &e) {
+    return fail(h, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+}
+
+void build_setup(HostSetup &s) {
+    s.p = s.K + 1;
+    s.nx = s.ex * s.K;
+    s.ny = s.ey * s.K + 1;
+    const int p = s.p;
+    s.xi.resize(p); s.w.resize(p); s.D.resize(p * p); s.Dw.resize(p * p);
+    pf_gll(s.K, s.xi.data(), s.w.data(), s.D.data());
+    for (int a = 0; a < p; ++a)
+        for (int c = 0; c < p; ++c) s.Dw[a * p + c] = s.w[a] * s.D[a * p + c];
+    s.hx.resize(s.ex); s.hy.resize(s.ey);
+    for (int e = 0; e < s.ex; ++e) s.hx[e] = s.xb[e + 1] - s.xb[e];
+    for (int e = 0; e < s.ey; ++e) s.hy[e] = s.yb[e + 1] - s.yb[e];
+    s.Kx.resize((size_t)s.nx * s.nx); s.Mx.resize(s.nx);
+    s.Ky.resize((size_t)s.ny * s.ny); s.My.resize(s.ny);
+    pf_operators_1d(s.ex, s.xb.data(), s.K, 1, s.Kx.data(), s.Mx.data());
+    pf_operators_1d(s.ey, s.yb.data(), s.K, 0, s.Ky.data(), s.My.data());
+    s.Sx.resize((size_t)s.nx * s.nx); s.Lx.resize(s.nx);
+    pf_fdm_1d(s.nx, s.Kx.data(), s.Mx.data(), nullptr, s.Sx.data(), s.Lx.data());
+    // the zero eigenvalue of the periodic operator is exact
+    for (auto &v : s.Lx) if (std::fabs(v) < 1e-11) v = 0.0;
+    const int ny = s.ny;
+    auto mask = [&](bool bot, bool top) {
+        std::vector<unsigned char> m(ny, 0);
+        if (bot) m[0] = 1;
+        if (top) m[ny - 1] = 1;
+        return m;
+    };
+    std::vector<unsigned char> masks[4] = {
+        mask(s.vrow0 >= 0, s.vrow1 >= 0),   // V
+        mask(false, false),                 // psi, phi
+        mask(false, true),                  // P: Dirichlet on the open side
+        mask(true, false)};                 // u: Dirichlet on the wall
+    for (int b = 0; b < 4; ++b) {
+        s.Sy[b].resize((size_t)ny * ny);
+        s.Ly[b].resize(ny);
+        pf_fdm_1d(ny, s.Ky.data(), s.My.data(), masks[b].data(), s.Sy[b].data(), s.Ly[b].data());
+        for (auto &v : s.Ly[b]) if (std::fabs(v) < 1e-11) v = 0.0;
+    }
+    // lifting of the potential's Dirichlet values: K_y[i][d] * V_d (times M_x in the kernel)
+    s.liftV.assign(ny, 0.0);
+    for (int i = 0; i < ny; ++i) {
+        if (s.vrow0 >= 0) s.liftV[i] += s.Ky[(size_t)i * ny + 0] * s.v0;
+        if (s.vrow1 >= 0) s.liftV[i] += s.Ky[(size_t)i * ny + (ny - 1)] * s.v1;
+    }
+    s.X.resize(s.nx);
+    for (int e = 0; e < s.ex; ++e)
+        for (int a = 0; a < s.K; ++a) s.X[e * s.K + a] = s.xb[e] + 0.5 * (s.xi[a] + 1.0) * s.hx[e];
+    s.Y.resize(ny);
+    for (int e = 0; e < s.ey; ++e)
+        for (int b = 0; b <= s.K; ++b) s.Y[e * s.K + b] = s.yb[e] + 0.5 * (s.xi[b] + 1.0) * s.hy[e];
+}
+
+// initial potential: fixed point of the Remark in Sec. 3.1 in FP64, run to the round-off
+// floor: stop when the max-norm update is <= 1e-15 vmax, or once it is below 1e-11 vmax and
+// no longer decreases, or after 20000 iterations (vmax = max(1, |electrode voltages|)).
+int initial_potential(pf_handle *h, Engine<double> &E, const double *phi0_dev) {
+    const double tol = 1e-15;
+    double prev = INFINITY;
+    double vmax = 1.0;
+    if (h->hs.vrow0 >= 0) vmax = std::max(vmax, std::fabs(h->hs.v0));
+    if (h->hs.vrow1 >= 0) vmax = std::max(vmax, std::fabs(h->hs.v1));
+    int a = 0;   // slot of the current iterate
+    PF_CU(cudaMemsetAsync(E.V[0], 0, E.N * sizeof(double), E.st));
+    if (E.d3) PF_CU(cudaMemsetAsync(E.Ez[0], 0, E.N * sizeof(double), E.st));
+    int it = 0;
+    for (it = 1; it <= 20000; ++it) {
+        E.potential(1, phi0_dev, phi0_dev, E.V[a], E.V[a], E.Ez[a], E.Ez[a], E.V[1 - a], E.Ez[1 - a]);
+        const double diff = E.reduce(E.V[1 - a], E.V[a], 2);
+        a = 1 - a;
+        if (!(diff == diff)) return fail(h, PF_EDIVERGED, "non-finite value in the initial potential");
+        if (diff <= tol * vmax || (diff <= 1e-11 * vmax && diff >= prev)) break;
+        prev = diff;
+    }
+    h->v_iters = std::min(it, 20000);
+    if (a != 0) {
+        PF_CU(cudaMemcpyAsync(E.V[0], E.V[1], E.N * sizeof(double), cudaMemcpyDeviceToDevice, E.st));
+        if (E.d3) PF_CU(cudaMemcpyAsync(E.Ez[0], E.Ez[1], E.N * sizeof(double), cudaMemcpyDeviceToDevice, E.st));
+    }
+    return PF_OK;
+}
+
+template <typename T>
+void copy_level(Engine<T> &E, int from, int to) {
+    auto cp = [&](T *const *arr) {
+        if (arr[from] && arr[to]) PF_CU(cudaMemcpyAsync(arr[to], arr[from], E.N * sizeof(T), cudaMemcpyDeviceToDevice, E.st));
+    };
+    cp(E.V); cp(E.Ez); cp(E.phi); cp(E.dzphi); cp(E.P); cp(E.dzP);
+    for (int c = 0; c < 3; ++c) { cp(E.u[c]); cp(E.dzu[c]); }
+}
+
+template <typename T>
+void upload_field(Engine<T> &E, T *dst, const double *host) {
+    std::vector<T> h(host, host + E.N);
+    PF_CU(cudaMemcpyAsync(dst, h.data(), E.N * sizeof(T), cudaMemcpyHostToDevice, E.st));
+    PF_CU(cudaStreamSynchronize(E.st));
+}
+
+template <typename T>
+void download_field(Engine<T> &E, const T *src, double *host) {
+    std::vector<T> h(E.N);
+    PF_CU(cudaMemcpyAsync(h.data(), src, E.N * sizeof(T), cudaMemcpyDeviceToHost, E.st));
+    PF_CU(cudaStreamSynchronize(E.st));
+    for (long long i = 0; i < E.N; ++i) host[i] = (double)h[i];
+}
+
+// z-derivative of a physical field through the engine's own transforms (forward then
+// inverse with d/dz), used when a field is set from the host
+template <typename T>
+void dz_of(Engine<T> &E, const T *x, T *dzx) {
+    if (!E.d3) return;
+    E.fwd(x, 0, nullptr, 0, 0, 1.0, nullptr, E.RHS, nullptr);
+    E.inv(E.RHS, E.W1, dzx, -1, 0.0, -1, 0.0);
+}
+
+template <typename T>
+int engine_init_state(pf_handle *h, Engine<T> &E, const double *phi0, const double *u0) {
+    upload_field(E, E.phi[0], phi0);
+    dz_of(E, E.phi[0], E.dzphi[0]);
+    if (u0) {
+        for (int c = 0; c < (E.d3 ? 3 : 2); ++c) {
+            upload_field(E, E.u[c][0], u0 + c * E.N);
+            dz_of(E, E.u[c][0], E.dzu[c][0]);
+        }
+    }
+    return PF_OK;
+}
+
+template <typename T>
+int do_steps(pf_handle *h, Engine<T> &E, int nsteps) {
+    for (int s = 0; s < nsteps; ++s) {
+        const int J = (h->nstep == 0 || h->hs.bdf == 1) ? 1 : 2;
+        E.step(J);
+        h->last_J = J;
+        h->nstep += 1;
+        h->t += h->hs.dt;
+    }
+    return PF_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, const pf_scheme *scheme,
+                         const double *phi0, const double *u0, void *cuda_stream, pf_handle **out) {
+    if (out) *out = nullptr;
+    if (!mesh || !fluid || !vbc || !scheme || !phi0 || !out) return fail(nullptr, PF_EINVAL, "null argument");
+    if (mesh->ex < 1 || mesh->ey < 1 || !mesh->xb || !mesh->yb) return fail(nullptr, PF_EINVAL, "bad element counts");
+    if (mesh->order < 2 || mesh->order > 15) return fail(nullptr, PF_EINVAL, "order must be in [2, 15]");
+    if (mesh->nz < 1 || (mesh->nz > 1 && ((mesh->nz & (mesh->nz - 1)) != 0 || mesh->nz > 1024)))
+        return fail(nullptr, PF_EINVAL, "nz must be 1 or a power of two <= 1024");
+    if (mesh->nz > 1 && !(mesh->lz > 0)) return fail(nullptr, PF_EINVAL, "lz must be positive");
+    if (mesh->ex * mesh->order < 2) return fail(nullptr, PF_EINVAL, "need at least 2 nodes in x");
+    for (int e = 0; e < mesh->ex; ++e)
+        if (!(mesh->xb[e + 1] > mesh->xb[e])) return fail(nullptr, PF_EINVAL, "xb must increase");
+    for (int e = 0; e < mesh->ey; ++e)
+        if (!(mesh->yb[e + 1] > mesh->yb[e])) return fail(nullptr, PF_EINVAL, "yb must increase");
+    if (vbc->bottom_kind != PF_BC_DIRICHLET && vbc->bottom_kind != PF_BC_NEUMANN) return fail(nullptr, PF_EINVAL, "bad bottom_kind");
+    if (vbc->top_kind != PF_BC_DIRICHLET && vbc->top_kind != PF_BC_NEUMANN) return fail(nullptr, PF_EINVAL, "bad top_kind");
+    if (vbc->bottom_kind == PF_BC_NEUMANN && vbc->top_kind == PF_BC_NEUMANN)
+        return fail(nullptr, PF_EINVAL, "the potential needs an electrode (Dirichlet) on at least one side");
+    const pf_fluid &f = *fluid;
+    if (!(f.rho1 > 0 && f.rho2 > 0 && f.mu1 > 0 && f.mu2 > 0 && f.eps1 > 0 && f.eps2 > 0 && f.sigma >= 0 &&
+          f.eta > 0 && f.gamma1 > 0))
+        return fail(nullptr, PF_EINVAL, "fluid parameters must be positive");
+    if (!(scheme->dt > 0) || (scheme->bdf != 1 && scheme->bdf != 2)) return fail(nullptr, PF_EINVAL, "bad dt or bdf");
+    if (scheme->precision != PF_FP64 && scheme->precision != PF_MIXED) return fail(nullptr, PF_EINVAL, "bad precision");
+
+    std::unique_ptr<pf_handle> h(new pf_handle());
+    HostSetup &s = h->hs;
+    s.ex = mesh->ex; s.ey = mesh->ey; s.K = mesh->order; s.nz = mesh->nz; s.lz = mesh->nz > 1 ? mesh->lz : 1.0;
+    s.xb.assign(mesh->xb, mesh->xb + s.ex + 1);
+    s.yb.assign(mesh->yb, mesh->yb + s.ey + 1);
+    s.rho1 = f.rho1; s.rho2 = f.rho2; s.mu1 = f.mu1; s.mu2 = f.mu2; s.eps1 = f.eps1; s.eps2 = f.eps2;
+    s.sigma = f.sigma; s.eta = f.eta; s.gamma1 = f.gamma1; s.theta = f.theta_s_deg;
+    s.dt = scheme->dt; s.bdf = scheme->bdf; s.precision = scheme->precision;
+    // Sec. 2.1 and Sec. 3.1 constants (same formulas and order of operations as documented in pf.h)
+    s.lam = 3.0 * s.sigma * s.eta / (2.0 * std::sqrt(2.0));
+    s.eps0 = scheme->eps0 != 0.0 ? scheme->eps0 : std::max(s.eps1, s.eps2);
+    s.rho0 = scheme->rho0 != 0.0 ? scheme->rho0 : std::min(s.rho1, s.rho2);
+    s.nu_m = scheme->nu_m != 0.0 ? scheme->nu_m : std::max(s.mu1, s.mu2) / std::min(s.rho1, s.rho2);
+    if (scheme->S != 0.0) s.S = scheme->S;
+    else {
+        const double g0 = s.bdf == 2 ? 1.5 : 1.0;
+        s.S = std::pow(s.eta, 2.0) * std::sqrt(4.0 * g0 / (s.lam * s.gamma1 * s.dt));
+    }
+    s.cos_theta = std::cos(s.theta * M_PI / 180.0);
+    if (vbc->bottom_kind == PF_BC_DIRICHLET) { s.vrow0 = 0; s.v0 = vbc->v_bottom; }
+    if (vbc->top_kind == PF_BC_DIRICHLET) { s.vrow1 = s.ey * s.K; s.v1 = vbc->v_top; }
+    build_setup(s);
+    h->st = (cudaStream_t)cuda_stream;
+    try {
+        // the initial potential always runs in FP64
+        std::unique_ptr<Engine<double>> e64(new Engine<double>(s, h->st));
+        engine_init_state(h.get(), *e64, phi0, u0);
+        int rc = initial_potential(h.get(), *e64, e64->phi[0]);
+        if (rc != PF_OK) { g_create_error = h->err; return rc; }
+        e64->efield(e64->V[0]);
+        copy_level(*e64, 0, 1);
+        e64->cur = 0;
+        if (s.precision == PF_FP64) {
+            h->e64 = std::move(e64);
+        } else {
+            std::unique_ptr<Engine<float>> e32(new Engine<float>(s, h->st));
+            auto cv = [&](const double *src, float *dst) {
+                if (!src || !dst) return;
+                pf::k_convert<double, float><<<1024, 256, 0, h->st>>>(src, dst, e64->N);
+            };
+            for (int l = 0; l < 2; ++l) {
+                cv(e64->V[l], e32->V[l]); cv(e64->Ez[l], e32->Ez[l]); cv(e64->phi[l], e32->phi[l]);
+                cv(e64->dzphi[l], e32->dzphi[l]); cv(e64->P[l], e32->P[l]); cv(e64->dzP[l], e32->dzP[l]);
+                for (int c = 0; c < 3; ++c) { cv(e64->u[c][l], e32->u[c][l]); cv(e64->dzu[c][l], e32->dzu[c][l]); }
+            }
+            cv(e64->Ex, e32->Ex); cv(e64->Ey, e32->Ey);
+            PF_CU(cudaGetLastError());
+            PF_CU(cudaStreamSynchronize(h->st));
+            e64.reset();
+            h->e32 = std::move(e32);
+        }
+    } catch (const CudaError &e) {
+        g_create_error = e.where + ": " + cudaGetErrorString(e.code);
+        return e.code == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
+    }
+    *out = h.release();
+    return PF_OK;
+}
+
+extern "C" int pf_step(pf_handle *h, int nsteps) {
+    if (!h) return PF_EINVAL;
+    if (nsteps < 0) return fail(h, PF_EINVAL, "nsteps must be >= 0");
+    try {
+        if (h->e64) return do_steps(h, *h->e64, nsteps);
+        return do_steps(h, *h->e32, nsteps);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+namespace {
+template <typename T>
+int sync_impl(pf_handle *h, Engine<T> &E) {
+    PF_CU(cudaStreamSynchronize(E.st));
+    const int n = E.cur;
+    double m = E.reduce(E.phi[n], nullptr, 1);
+    double um = 0.0;
+    for (int c = 0; c < 3; ++c)
+        if (E.u[c][n]) um = std::max(um, E.reduce(E.u[c][n], nullptr, 1));
+    if (!(m == m) || !(um == um) || std::isinf(m) || std::isinf(um)) h->diverged = true;
+    return h->diverged ? fail(h, PF_EDIVERGED, "non-finite value in the state") : PF_OK;
+}
+}  // namespace
+
+extern "C" int pf_sync(pf_handle *h) {
+    if (!h) return PF_EINVAL;
+    try {
+        if (h->e64) return sync_impl(h, *h->e64);
+        return sync_impl(h, *h->e32);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+namespace {
+template <typename T>
+int get_impl(pf_handle *h, Engine<T> &E, unsigned mask, double *out, size_t n) {
+    const bool old = mask & PF_FIELD_OLD;
+    const int l = old ? 1 - E.cur : E.cur;
+    size_t need = 0;
+    if (mask & PF_FIELD_V) need += 1;
+    if (mask & PF_FIELD_E) need += 3;
+    if (mask & PF_FIELD_PHI) need += 1;
+    if (mask & PF_FIELD_PSI) need += 1;
+    if (mask & PF_FIELD_P) need += 1;
+    if (mask & PF_FIELD_U) need += 3;
+    if (need * (size_t)E.N > n) return fail(h, PF_EINVAL, "output buffer too small");
+    PF_CU(cudaStreamSynchronize(E.st));
+    double *o = out;
+    auto put = [&](const T *src) {
+        if (src) download_field(E, src, o);
+        else std::fill(o, o + E.N, 0.0);
+        o += E.N;
+    };
+    if (mask & PF_FIELD_V) put(E.V[l]);
+    if (mask & PF_FIELD_E) { put(E.Ex); put(E.Ey); put(E.d3 ? E.Ez[E.cur] : nullptr); }
+    if (mask & PF_FIELD_PHI) put(E.phi[l]);
+    if (mask & PF_FIELD_PSI) {
+        // psi = L + alpha phi, L = psi - alpha phi of the last step
+        std::vector<double> phi(E.N);
+        download_field(E, E.phi[E.cur], phi.data());
+        download_field(E, E.Lf, o);
+        const double al = alpha_of(h->hs, h->last_J);
+        for (long long i = 0; i < E.N; ++i) o[i] += al * phi[i];
+        o += E.N;
+    }
+    if (mask & PF_FIELD_P) put(E.P[l]);
+    if (mask & PF_FIELD_U) { put(E.u[0][l]); put(E.u[1][l]); put(E.u[2][l]); }
+    return PF_OK;
+}
+
+template <typename T>
+int set_impl(pf_handle *h, Engine<T> &E, unsigned mask, const double *in, size_t n, int reset) {
+    const bool old = mask & PF_FIELD_OLD;
+    const int l = old ? 1 - E.cur : E.cur;
+    size_t need = 0;
+    if (mask & PF_FIELD_V) need += 1;
+    if (mask & PF_FIELD_E) return fail(h, PF_EINVAL, "E is derived from V and cannot be set");
+    if (mask & PF_FIELD_PSI) return fail(h, PF_EINVAL, "psi cannot be set");
+    if (mask & PF_FIELD_PHI) need += 1;
+    if (mask & PF_FIELD_P) need += 1;
+    if (mask & PF_FIELD_U) need += 3;
+    if (need * (size_t)E.N > n) return fail(h, PF_EINVAL, "input buffer too small");
+    const double *p = in;
+    auto take = [&](T *dst, T *dzdst) {
+        if (dst) {
+            upload_field(E, dst, p);
+            if (dzdst) dz_of(E, dst, dzdst);
+        }
+        p += E.N;
+    };
+    if (mask & PF_FIELD_V) take(E.V[l], E.d3 ? E.Ez[l] : nullptr);
+    if (mask & PF_FIELD_PHI) take(E.phi[l], E.d3 ? E.dzphi[l] : nullptr);
+    if (mask & PF_FIELD_P) take(E.P[l], E.d3 ? E.dzP[l] : nullptr);
+    if (mask & PF_FIELD_U)
+        for (int c = 0; c < 3; ++c) take(E.u[c][l], E.d3 ? E.dzu[c][l] : nullptr);
+    if (mask & PF_FIELD_V && !old) E.efield(E.V[l]);
+    if (reset) {
+        copy_level(E, E.cur, 1 - E.cur);
+        h->nstep = 0;
+    }
+    PF_CU(cudaStreamSynchronize(E.st));
+    return PF_OK;
+}
+}  // namespace
+
+extern "C" int pf_get_fields(pf_handle *h, unsigned mask, double *host_out, size_t n) {
+    if (!h || !host_out) return PF_EINVAL;
+    try {
+        if (h->e64) return get_impl(h, *h->e64, mask, host_out, n);
+        return get_impl(h, *h->e32, mask, host_out, n);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+extern "C" int pf_set_fields(pf_handle *h, unsigned mask, const double *host_in, size_t n, int reset_history) {
+    if (!h || !host_in) return PF_EINVAL;
+    try {
+        if (h->e64) return set_impl(h, *h->e64, mask, host_in, n, reset_history);
+        return set_impl(h, *h->e32, mask, host_in, n, reset_history);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+namespace {
+template <typename T>
+int diag_impl(pf_handle *h, Engine<T> &E, double *out) {
+    PF_CU(cudaStreamSynchronize(E.st));
+    const int n = E.cur;
+    const double plane_w = E.d3 ? h->hs.lz / E.nz : 1.0;
+    out[0] = E.reduce(E.phi[n], nullptr, 0) * plane_w;
+    double um = 0.0;
+    for (int c = 0; c < 3; ++c)
+        if (E.u[c][n]) {
+            const double v = E.reduce(E.u[c][n], nullptr, 1);
+            um = (v != v) ? v : std::max(um, v);
+        }
+    out[1] = um;
+    out[2] = h->t;
+    out[3] = (double)h->nstep;
+    out[4] = h->v_iters;
+    if (!(out[0] == out[0]) || !(um == um)) h->diverged = true;
+    out[5] = h->diverged ? 1.0 : 0.0;
+    out[6] = out[7] = 0.0;
+    return PF_OK;
+}
+
+template <typename T>
+int helm_impl(pf_handle *h, Engine<T> &E, int bcset, int mode, double lambda, const double *rhs, double *out) {
+    const int np = mode == 0 ? 1 : 2;
+    const HostSetup &s = h->hs;
+    std::vector<T> b((size_t)np * E.n2);
+    for (int pl = 0; pl < np; ++pl)
+        for (int i = 0; i < E.ny; ++i)
+            for (int j = 0; j < E.nx; ++j) {
+                const size_t q = (size_t)i * E.nx + j;
+                b[(size_t)pl * E.n2 + q] = (T)(s.Mx[j] * s.My[i] * rhs[(size_t)pl * E.n2 + q]);
+            }
+    const double beta = E.d3 ? 2.0 * M_PI * mode / s.lz : 0.0;
+    std::vector<T> sh(3 * E.nz, (T)(lambda + beta * beta));
+    PF_CU(cudaMemcpyAsync(E.shTmp, sh.data(), sh.size() * sizeof(T), cudaMemcpyHostToDevice, E.st));
+    PF_CU(cudaMemcpyAsync(E.RHS, b.data(), b.size() * sizeof(T), cudaMemcpyHostToDevice, E.st));
+    E.fdm(E.RHS, E.OUT, bcset, E.shTmp, np);
+    std::vector<T> o((size_t)np * E.n2);
+    PF_CU(cudaMemcpyAsync(o.data(), E.OUT, o.size() * sizeof(T), cudaMemcpyDeviceToHost, E.st));
+    PF_CU(cudaStreamSynchronize(E.st));
+    for (size_t i = 0; i < o.size(); ++i) out[i] = (double)o[i];
+    return PF_OK;
+}
+}  // namespace
+
+extern "C" int pf_diagnostics(pf_handle *h, double out[8]) {
+    if (!h || !out) return PF_EINVAL;
+    try {
+        if (h->e64) return diag_impl(h, *h->e64, out);
+        return diag_impl(h, *h->e32, out);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+extern "C" int pf_solve_helmholtz(pf_handle *h, int bcset, int mode, double lambda, const double *rhs, double *out) {
+    if (!h || !rhs || !out) return PF_EINVAL;
+    if (bcset < 0 || bcset > 3) return fail(h, PF_EINVAL, "bcset must be one of PF_BCSET_*");
+    if (mode < 0 || (h->hs.nz == 1 && mode != 0) || (h->hs.nz > 1 && mode > h->hs.nz / 2))
+        return fail(h, PF_EINVAL, "mode out of range");
+    try {
+        if (h->e64) return helm_impl(h, *h->e64, bcset, mode, lambda, rhs, out);
+        return helm_impl(h, *h->e32, bcset, mode, lambda, rhs, out);
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+}
+
+extern "C" int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]) {
+    if (!h) return PF_EINVAL;
+    const HostSetup &s = h->hs;
+    if (nodes_x) std::copy(s.X.begin(), s.X.end(), nodes_x);
+    if (nodes_y) std::copy(s.Y.begin(), s.Y.end(), nodes_y);
+    if (dims) {
+        dims[0] = s.nx; dims[1] = s.ny; dims[2] = s.nz;
+        dims[3] = s.nx * s.ny * s.nz;
+    }
+    return PF_OK;
+}
+
+extern "C" void pf_destroy(pf_handle *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    delete h;
+}
+
+extern "C" const char *pf_last_error(const pf_handle *h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}

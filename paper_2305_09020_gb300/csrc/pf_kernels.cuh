@@ -1,0 +1,846 @@
+// CUDA kernels of the per-step path (sm_103a), templated on the working precision T.
+//
+// Data layout in HBM
+//   nodal fields  [z][y][x]            n2 = n_y * n_x values per plane, x fastest
+//   element-local [z][ey][ex][b][a]    (K+1)^2 slots per element (discontinuous data,
+//                                      weak-form contributions before direct
+//                                      stiffness summation)
+//   mode planes   [p][y][x]            real FFT along z packed into Nz real planes:
+//                                      p = 0: Re(k = 0), p = 1: Re(k = Nz/2),
+//                                      p = 2k: Re(k), p = 2k+1: Im(k), 0 < k < Nz/2
+//
+// Kernels
+//   k_potential  RHS of eq. 54a/74a (weak form of the variable-permittivity correction)
+//   k_efield     E = M^{-1} (assembled weighted derivative of V), eq. 55/78
+//   k_chem       Q1, Q2 and the psi right-hand side, eq. 56/75
+//   k_momentum   T, G (eq. 49), the pressure RHS (eq. 58/77) and the velocity RHS
+//                except its new-pressure term (eq. 59/78)
+//   k_ugradp     the -(1/(nu_m rho0)) grad P^{n+1} term of eq. 59/78
+//   k_fwd        direct stiffness summation + z real FFT + (A + m_k B) combination,
+//                scaling and Dirichlet lifting  -> mode-plane right-hand sides
+//   k_inv        inverse z FFT of a mode-plane solution (value and d/dz), Dirichlet
+//                values; variant for phi that also forms psi - alpha phi combinations
+//   k_gemm       C = A B with a small shared B (fast-diagonalisation transforms) and
+//                an epilogue that divides by the eigenvalue sum or stores transposed
+//   reductions   FP64 phase mass, max |u|, max |difference|
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pf {
+
+template <typename T>
+struct cplx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+template <typename T>
+struct Geo {
+    int ex, ey, K, p, nx, ny, n2, nz;
+    const T *hx, *hy;   // element sizes
+    const T *D;         // D[a*p+m] = l_m'(xi_a)
+    const T *Dw;        // Dw[a*p+c] = w_a D[a*p+c]
+    const T *w;         // GLL weights
+    const T *Mx, *My;   // assembled 1D masses
+};
+
+template <typename T>
+struct Phys {
+    T rho1, rho2, mu1, mu2, eps1, eps2;
+    T lam, inv_eta2, gamma1, S_eta2, eps0, rho0, nu_m, dt, sigma, cos_theta;
+    T alpha, gamma0;
+    int J;
+    int wetting;   // theta_s != 90 degrees
+};
+
+// ---- mixture laws (eq. interpolation) and free-energy pieces (Sec. 2.1) -------------------
+template <typename T> __device__ __forceinline__ T rho_of(const Phys<T> &q, T phi) {
+    return T(0.5) * (q.rho1 + q.rho2) + T(0.5) * (q.rho1 - q.rho2) * phi;
+}
+template <typename T> __device__ __forceinline__ T mu_of(const Phys<T> &q, T phi) {
+    return T(0.5) * (q.mu1 + q.mu2) + T(0.5) * (q.mu1 - q.mu2) * phi;
+}
+template <typename T> __device__ __forceinline__ T eps_of(const Phys<T> &q, T phi) {
+    return T(0.5) * (q.eps1 + q.eps2) + T(0.5) * (q.eps1 - q.eps2) * phi * (T(3) - phi * phi) * T(0.5);
+}
+template <typename T> __device__ __forceinline__ T deps_of(const Phys<T> &q, T phi) {
+    return T(0.5) * (q.eps2 - q.eps1) * T(3) * (phi * phi - T(1)) * T(0.5);
+}
+template <typename T> __device__ __forceinline__ T h_of(const Phys<T> &q, T phi) {
+    return phi * (phi * phi - T(1)) * q.inv_eta2;
+}
+template <typename T> __device__ __forceinline__ T dtheta_of(const Phys<T> &q, T phi) {
+    return q.sigma * q.cos_theta * T(3) * (phi * phi - T(1)) * T(0.25);
+}
+// BDF-J extrapolation xi* and the history term xi_hat (Sec. 3.1)
+template <typename T> __device__ __forceinline__ T star(int J, T a, T b) { return J == 1 ? a : T(2) * a - b; }
+template <typename T> __device__ __forceinline__ T hatv(int J, T a, T b) { return J == 1 ? a : T(2) * a - T(0.5) * b; }
+
+// ---- element helpers ----------------------------------------------------------------------
+struct ElemIdx {
+    int ex, ey, a, b, t, z;
+    long long g;    // global nodal index (with plane offset)
+    long long l;    // element-local slot (with plane offset)
+};
+
+template <typename T>
+__device__ __forceinline__ ElemIdx elem_index(const Geo<T> &G) {
+    ElemIdx e;
+    const int el = blockIdx.x;
+    e.z = blockIdx.y;
+    e.ex = el % G.ex;
+    e.ey = el / G.ex;
+    e.t = threadIdx.x;
+    e.a = e.t % G.p;
+    e.b = e.t / G.p;
+    int xi = e.ex * G.K + e.a;
+    if (xi >= G.nx) xi -= G.nx;
+    e.g = (long long)e.z * G.n2 + (long long)(e.ey * G.K + e.b) * G.nx + xi;
+    e.l = ((long long)e.z * G.ex * G.ey + el) * (G.p * G.p) + e.t;
+    return e;
+}
+
+// shared tables: D, Dw, w (loaded by every element kernel)
+template <typename T>
+__device__ __forceinline__ void load_tables(const Geo<T> &G, T *sD, T *sDw, T *sw) {
+    const int pp = G.p * G.p;
+    for (int i = threadIdx.x; i < pp; i += blockDim.x) {
+        sD[i] = G.D[i];
+        sDw[i] = G.Dw[i];
+    }
+    for (int i = threadIdx.x; i < G.p; i += blockDim.x) sw[i] = G.w[i];
+}
+
+// d/dx and d/dy of an element array f[b*p+a] at (a, b); scale = 2/h
+template <typename T>
+__device__ __forceinline__ T ddx(const T *f, const T *sD, int p, int a, int b, T sc) {
+    T s = 0;
+    for (int m = 0; m < p; ++m) s += sD[a * p + m] * f[b * p + m];
+    return s * sc;
+}
+template <typename T>
+__device__ __forceinline__ T ddy(const T *f, const T *sD, int p, int a, int b, T sc) {
+    T s = 0;
+    for (int m = 0; m < p; ++m) s += sD[b * p + m] * f[m * p + a];
+    return s * sc;
+}
+// weak forms: int F d(l_{a'b'})/dx and int F d(l_{a'b'})/dy over the element
+template <typename T>
+__device__ __forceinline__ T wdx(const T *F, const T *sDw, const T *sw, int p, int a, int b, T hy2) {
+    T s = 0;
+    for (int m = 0; m < p; ++m) s += sDw[m * p + a] * F[b * p + m];
+    return s * hy2 * sw[b];
+}
+template <typename T>
+__device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, int a, int b, T hx2) {
+    T s = 0;
+    for (int m = 0; m < p; ++m) s += sDw[m * p + b] * F[m * p + a];
+    return s * hx2 * sw[a];
+}
+
+#define PF_ELEM_SMEM(T, G, nfields)                                                   \
+    extern __shared__ unsigned char pf_smem_raw[];                                    \
+    T *sD = reinterpret_cast<T *>(pf_smem_raw);                                       \
+    T *sDw = sD + (G).p * (G).p;                                                      \
+    T *sw = sDw + (G).p * (G).p;                                                      \
+    T *sF = sw + 32;                                                                  \
+    const int pp_ = (G).p * (G).p;                                                    \
+    (void)pp_;
+
+// ---- eq. 54a / 74a: RHS of the potential --------------------------------------------------
+// A = -int R_2D . grad_2D w  (element-local contributions),  B = int R_z w  (iB multiplier)
+// with R = (eps(phi*) - eps0) grad V*.
+template <typename T>
+__global__ void k_potential(Geo<T> G, Phys<T> q, const T *__restrict__ phin, const T *__restrict__ phio,
+                            const T *__restrict__ Vn, const T *__restrict__ Vo, const T *__restrict__ Ezn,
+                            const T *__restrict__ Ezo, T *__restrict__ A, T *__restrict__ B) {
+    PF_ELEM_SMEM(T, G, 3)
+    T *sV = sF, *sRx = sF + pp_, *sRy = sF + 2 * pp_;
+    load_tables(G, sD, sDw, sw);
+    const ElemIdx e = elem_index(G);
+    const bool act = e.t < pp_;
+    const T hx = G.hx[e.ex], hy = G.hy[e.ey];
+    T phis = 0, Vs = 0;
+    if (act) {
+        phis = star(q.J, phin[e.g], phio[e.g]);
+        Vs = star(q.J, Vn[e.g], Vo[e.g]);
+        sV[e.t] = Vs;
+    }
+    __syncthreads();
+    T c = 0;
+    if (act) {
+        c = eps_of(q, phis) - q.eps0;
+        sRx[e.t] = c * ddx(sV, sD, G.p, e.a, e.b, T(2) / hx);
+        sRy[e.t] = c * ddy(sV, sD, G.p, e.a, e.b, T(2) / hy);
+    }
+    __syncthreads();
+    if (!act) return;
+    const T hx2 = T(0.5) * hx, hy2 = T(0.5) * hy;
+    A[e.l] = -(wdx(sRx, sDw, sw, G.p, e.a, e.b, hy2) + wdy(sRy, sDw, sw, G.p, e.a, e.b, hx2));
+    if (B) {
+        const T Ez = star(q.J, Ezn[e.g], Ezo[e.g]);
+        B[e.l] = hx2 * hy2 * sw[e.a] * sw[e.b] * c * Ez;
+    }
+}
+
+// ---- eq. 55 / 78: E_x, E_y = M^{-1} * sum over elements of M_e * (element derivative of V)
+// On a tensor mesh the y (resp. x) factors of M_e cancel, leaving a 1D weighted average.
+template <typename T>
+__global__ void k_efield(Geo<T> G, const T *__restrict__ V, T *__restrict__ Ex, T *__restrict__ Ey) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)G.n2 * G.nz;
+    if (gid >= tot) return;
+    const int z = (int)(gid / G.n2);
+    const int q = (int)(gid % G.n2);
+    const int i = q / G.nx, j = q % G.nx;
+    const T *Vp = V + (long long)z * G.n2;
+    const int p = G.p, K = G.K;
+    // x: elements containing column j
+    T sx = 0;
+    {
+        int exs[2], as[2], ne = 0;
+        if (j % K == 0) {
+            exs[ne] = j / K; as[ne++] = 0;
+            exs[ne] = (j / K - 1 + G.ex) % G.ex; as[ne++] = K;
+        } else {
+            exs[ne] = j / K; as[ne++] = j % K;
+        }
+        for (int c = 0; c < ne; ++c) {
+            T s = 0;
+            for (int m = 0; m < p; ++m) {
+                int xm = exs[c] * K + m;
+                if (xm >= G.nx) xm -= G.nx;
+                s += G.D[as[c] * p + m] * Vp[i * G.nx + xm];
+            }
+            sx += G.w[as[c]] * s;
+        }
+    }
+    T sy = 0;
+    {
+        int eys[2], bs[2], ne = 0;
+        if (i % K == 0) {
+            if (i > 0) { eys[ne] = i / K - 1; bs[ne++] = K; }
+            if (i < G.ny - 1) { eys[ne] = i / K; bs[ne++] = 0; }
+        } else {
+            eys[ne] = i / K; bs[ne++] = i % K;
+        }
+        for (int c = 0; c < ne; ++c) {
+            T s = 0;
+            for (int m = 0; m < p; ++m) s += G.D[bs[c] * p + m] * Vp[(eys[c] * K + m) * G.nx + j];
+            sy += G.w[bs[c]] * s;
+        }
+    }
+    Ex[gid] = sx / G.Mx[j];
+    Ey[gid] = sy / G.My[i];
+}
+
+// ---- eq. 56 / 75: psi right-hand side ----------------------------------------------------
+// Q1 = (-u* . grad phi* + phi_hat/dt)/(lambda gamma1) (element-local),
+// Q2 = h(phi*) - (S/eta^2) phi* - eps'(phi*)/(2 lambda) |E|^2 (nodal, written to Q2n),
+// A = -int Q1 w + int grad_2D Q2 . grad_2D w + (alpha + S/eta^2) int_wall U w,
+// U = -Theta'(phi*)/lambda; faceU (optional) = int_wall U w (element-local face slots).
+template <typename T>
+__global__ void k_chem(Geo<T> G, Phys<T> q, const T *__restrict__ phin, const T *__restrict__ phio,
+                       const T *__restrict__ dzphin, const T *__restrict__ dzphio,
+                       const T *__restrict__ uxn, const T *__restrict__ uxo, const T *__restrict__ uyn,
+                       const T *__restrict__ uyo, const T *__restrict__ uzn, const T *__restrict__ uzo,
+                       const T *__restrict__ Ex, const T *__restrict__ Ey, const T *__restrict__ Ez,
+                       T *__restrict__ A, T *__restrict__ Q2n, T *__restrict__ faceU) {
+    PF_ELEM_SMEM(T, G, 4)
+    T *sP = sF, *sQ = sF + pp_, *sQx = sF + 2 * pp_, *sQy = sF + 3 * pp_;
+    load_tables(G, sD, sDw, sw);
+    const ElemIdx e = elem_index(G);
+    const bool act = e.t < pp_;
+    const T hx = G.hx[e.ex], hy = G.hy[e.ey];
+    T phis = 0, Q1 = 0;
+    if (act) {
+        phis = star(q.J, phin[e.g], phio[e.g]);
+        sP[e.t] = phis;
+        const T ex = Ex[e.g], ey = Ey[e.g], ez = Ez ? Ez[e.g] : T(0);
+        const T E2 = ex * ex + ey * ey + ez * ez;
+        const T Q2 = h_of(q, phis) - q.S_eta2 * phis - deps_of(q, phis) / (T(2) * q.lam) * E2;
+        sQ[e.t] = Q2;
+        Q2n[e.g] = Q2;   // identical value from every element sharing the node
+    }
+    __syncthreads();
+    if (act) {
+        const T sx = T(2) / hx, sy = T(2) / hy;
+        const T gpx = ddx(sP, sD, G.p, e.a, e.b, sx);
+        const T gpy = ddy(sP, sD, G.p, e.a, e.b, sy);
+        T adv = star(q.J, uxn[e.g], uxo[e.g]) * gpx + star(q.J, uyn[e.g], uyo[e.g]) * gpy;
+        if (uzn) adv += star(q.J, uzn[e.g], uzo[e.g]) * star(q.J, dzphin[e.g], dzphio[e.g]);
+        const T phh = hatv(q.J, phin[e.g], phio[e.g]);
+        Q1 = (-adv + phh / q.dt) / (q.lam * q.gamma1);
+        sQx[e.t] = ddx(sQ, sD, G.p, e.a, e.b, sx);
+        sQy[e.t] = ddy(sQ, sD, G.p, e.a, e.b, sy);
+    }
+    __syncthreads();
+    if (!act) return;
+    const T hx2 = T(0.5) * hx, hy2 = T(0.5) * hy;
+    T r = -hx2 * hy2 * sw[e.a] * sw[e.b] * Q1 + wdx(sQx, sDw, sw, G.p, e.a, e.b, hy2) +
+          wdy(sQy, sDw, sw, G.p, e.a, e.b, hx2);
+    if (q.wetting && e.ey == 0 && e.b == 0) {
+        const T U = -dtheta_of(q, phis) / q.lam;
+        const T fu = hx2 * sw[e.a] * U;
+        r += (q.alpha + q.S_eta2) * fu;
+        if (faceU) faceU[((long long)e.z * G.ex + e.ex) * G.p + e.a] = fu;
+    }
+    A[e.l] = r;
+}
+
+// ---- eq. 49, 58a / 77a, 59a / 78a: momentum right-hand sides -------------------------------
+// T = (1/rho)[-lambda L grad phi - eps'(phi)/2 |E|^2 grad phi + grad mu . D(u*) - Jt . grad u*]
+//     + u_hat/dt - u* . grad u* + (1/rho0 - 1/rho) grad P*,     L = psi - alpha phi,
+// Jt = (rho1 - rho2)/2 lambda gamma1 grad W,  G = T + grad(mu/rho) x omega*.
+// Outputs (element-local): AP = rho0 int G_2D . grad_2D q + wall term,  BP = -rho0 int G_z q + wall,
+// AU[c], BU[c]: the velocity right-hand side without the new pressure gradient.
+template <typename T>
+struct MomIn {
+    const T *phi, *dzphi, *W, *dzW, *L, *Ex, *Ey, *Ez;
+    const T *un[3], *uo[3], *dzun[3], *dzuo[3];
+    const T *Pn, *Po, *dzPn, *dzPo;
+};
+template <typename T>
+struct MomOut {
+    T *AP, *BP, *AU[3], *BU[3];
+};
+
+template <typename T>
+__global__ void k_momentum(Geo<T> G, Phys<T> q, MomIn<T> in, MomOut<T> out) {
+    PF_ELEM_SMEM(T, G, 6)
+    // inputs with in-plane derivatives: phi, W, u*_x, u*_y, u*_z, P*
+    T *sphi = sF, *sW = sF + pp_, *sux = sF + 2 * pp_, *suy = sF + 3 * pp_, *suz = sF + 4 * pp_,
+      *sPs = sF + 5 * pp_;
+    // fluxes for weak derivatives (reuse after the derivative pass)
+    T *sGx = sF + 6 * pp_, *sGy = sF + 7 * pp_, *sKx = sF + 8 * pp_, *sKy = sF + 9 * pp_,
+      *sKz = sF + 10 * pp_, *sJx = sF + 11 * pp_;
+    load_tables(G, sD, sDw, sw);
+    const ElemIdx e = elem_index(G);
+    const bool act = e.t < pp_;
+    const bool d3 = in.un[2] != nullptr;
+    const int J = q.J;
+    const T hx = G.hx[e.ex], hy = G.hy[e.ey];
+    T us[3] = {0, 0, 0};
+    if (act) {
+        sphi[e.t] = in.phi[e.g];
+        sW[e.t] = in.W[e.g];
+        us[0] = star(J, in.un[0][e.g], in.uo[0][e.g]);
+        us[1] = star(J, in.un[1][e.g], in.uo[1][e.g]);
+        if (d3) us[2] = star(J, in.un[2][e.g], in.uo[2][e.g]);
+        sux[e.t] = us[0];
+        suy[e.t] = us[1];
+        suz[e.t] = us[2];
+        sPs[e.t] = star(J, in.Pn[e.g], in.Po[e.g]);
+    }
+    __syncthreads();
+    T mr = 0, om[3] = {0, 0, 0}, Gv[3] = {0, 0, 0};
+    if (act) {
+        const T sx = T(2) / hx, sy = T(2) / hy;
+        const T phi = sphi[e.t];
+        T gphi[3] = {ddx(sphi, sD, G.p, e.a, e.b, sx), ddy(sphi, sD, G.p, e.a, e.b, sy),
+                     d3 ? in.dzphi[e.g] : T(0)};
+        T gW[3] = {ddx(sW, sD, G.p, e.a, e.b, sx), ddy(sW, sD, G.p, e.a, e.b, sy), d3 ? in.dzW[e.g] : T(0)};
+        T gu[3][3];   // gu[c][d] = d u*_c / d x_d
+        gu[0][0] = ddx(sux, sD, G.p, e.a, e.b, sx);
+        gu[0][1] = ddy(sux, sD, G.p, e.a, e.b, sy);
+        gu[1][0] = ddx(suy, sD, G.p, e.a, e.b, sx);
+        gu[1][1] = ddy(suy, sD, G.p, e.a, e.b, sy);
+        gu[2][0] = d3 ? ddx(suz, sD, G.p, e.a, e.b, sx) : T(0);
+        gu[2][1] = d3 ? ddy(suz, sD, G.p, e.a, e.b, sy) : T(0);
+        if (d3) {
+            for (int c = 0; c < 3; ++c) gu[c][2] = star(J, in.dzun[c][e.g], in.dzuo[c][e.g]);
+        } else {
+            gu[0][2] = gu[1][2] = gu[2][2] = 0;
+        }
+        T gP[3] = {ddx(sPs, sD, G.p, e.a, e.b, sx), ddy(sPs, sD, G.p, e.a, e.b, sy),
+                   d3 ? star(J, in.dzPn[e.g], in.dzPo[e.g]) : T(0)};
+        const T rho = rho_of(q, phi), mu = mu_of(q, phi);
+        const T irho = T(1) / rho;
+        mr = mu * irho;
+        const T ex = in.Ex[e.g], ey = in.Ey[e.g], ez = d3 ? in.Ez[e.g] : T(0);
+        const T E2 = ex * ex + ey * ey + ez * ez;
+        const T Lv = in.L[e.g];
+        const T dmu = T(0.5) * (q.mu1 - q.mu2);
+        const T drho = T(0.5) * (q.rho1 - q.rho2);
+        const T cJ = drho * q.lam * q.gamma1;
+        const T kf = -q.lam * Lv - T(0.5) * deps_of(q, phi) * E2;
+        T uh[3];
+        for (int c = 0; c < 3; ++c) uh[c] = (c < 2 || d3) ? hatv(J, in.un[c][e.g], in.uo[c][e.g]) : T(0);
+        T Tv[3];
+        for (int c = 0; c < 3; ++c) {
+            T visc = 0, jgu = 0, conv = 0;
+            for (int d = 0; d < 3; ++d) {
+                visc += dmu * gphi[d] * (gu[c][d] + gu[d][c]);
+                jgu += cJ * gW[d] * gu[c][d];
+                conv += us[d] * gu[c][d];
+            }
+            Tv[c] = (kf * gphi[c] + visc - jgu) * irho + uh[c] / q.dt - conv + (T(1) / q.rho0 - irho) * gP[c];
+        }
+        om[0] = gu[2][1] - gu[1][2];
+        om[1] = gu[0][2] - gu[2][0];
+        om[2] = gu[1][0] - gu[0][1];
+        const T dmr = (dmu * rho - mu * drho) * irho * irho;
+        const T gm[3] = {dmr * gphi[0], dmr * gphi[1], dmr * gphi[2]};
+        Gv[0] = Tv[0] + gm[1] * om[2] - gm[2] * om[1];
+        Gv[1] = Tv[1] + gm[2] * om[0] - gm[0] * om[2];
+        Gv[2] = Tv[2] + gm[0] * om[1] - gm[1] * om[0];
+    }
+    __syncthreads();   // derivative inputs consumed; flux arrays written next
+    const T Kf = mr - q.nu_m;
+    if (act) {
+        sGx[e.t] = Gv[0];
+        sGy[e.t] = Gv[1];
+        sKx[e.t] = Kf * om[0];
+        sKy[e.t] = Kf * om[1];
+        sKz[e.t] = Kf * om[2];
+        sJx[e.t] = mr * om[2];   // wall: -J_x = (mu/rho) omega_z for n = (0,-1,0)
+    }
+    __syncthreads();
+    if (!act) return;
+    const T hx2 = T(0.5) * hx, hy2 = T(0.5) * hy;
+    const T Me = hx2 * hy2 * sw[e.a] * sw[e.b];
+    const T inu = T(1) / q.nu_m;
+    const int p = G.p;
+    // pressure: rho0 int G_2D . grad q - rho0 int_wall J_x dq/dx  ;  iB part: -rho0 int G_z q + rho0 int_wall J_z q
+    T ap = q.rho0 * (wdx(sGx, sDw, sw, p, e.a, e.b, hy2) + wdy(sGy, sDw, sw, p, e.a, e.b, hx2));
+    T bp = -q.rho0 * Me * Gv[2];
+    if (e.ey == 0 && e.b == 0) {
+        // -rho0 int_wall J_x dq/dx with J_x = -(mu/rho) omega_z: 1D weak x-derivative of the face row
+        T s = 0;
+        for (int m = 0; m < p; ++m) s += sDw[m * p + e.a] * sJx[m];   // row b = 0
+        ap += q.rho0 * s;
+        bp += q.rho0 * hx2 * sw[e.a] * mr * om[0];                     // J_z = (mu/rho) omega_x
+    }
+    out.AP[e.l] = ap;
+    if (out.BP) out.BP[e.l] = bp;
+    // velocity (without the new pressure): (1/nu_m) int G v - (1/nu_m) int K x grad v - (1/nu_m) int_top L v
+    T ax = inu * (Me * Gv[0] + wdy(sKz, sDw, sw, p, e.a, e.b, hx2));
+    T ay = inu * (Me * Gv[1] - wdx(sKz, sDw, sw, p, e.a, e.b, hy2));
+    T az = inu * (Me * Gv[2] - wdy(sKx, sDw, sw, p, e.a, e.b, hx2) + wdx(sKy, sDw, sw, p, e.a, e.b, hy2));
+    if (e.ey == G.ey - 1 && e.b == G.K) {
+        ax -= inu * hx2 * sw[e.a] * Kf * om[2];      // L_x = (mu/rho - nu_m) omega_z
+        az += inu * hx2 * sw[e.a] * Kf * om[0];      // L_z = -(mu/rho - nu_m) omega_x
+    }
+    out.AU[0][e.l] = ax;
+    out.AU[1][e.l] = ay;
+    if (d3) {
+        out.AU[2][e.l] = az;
+        out.BU[0][e.l] = inu * Me * Kf * om[1];       //  i beta (1/nu_m) int K_y v
+        out.BU[1][e.l] = -inu * Me * Kf * om[0];      // -i beta (1/nu_m) int K_x v
+    }
+}
+
+// -(1/(nu_m rho0)) int grad P^{n+1} v: added to AU[0], AU[1]; the z part is -(1/(nu_m rho0)) i beta int P v.
+template <typename T>
+__global__ void k_ugradp(Geo<T> G, Phys<T> q, const T *__restrict__ P, T *__restrict__ AUx,
+                         T *__restrict__ AUy, T *__restrict__ BUz) {
+    PF_ELEM_SMEM(T, G, 1)
+    T *sPv = sF;
+    load_tables(G, sD, sDw, sw);
+    const ElemIdx e = elem_index(G);
+    const bool act = e.t < pp_;
+    if (act) sPv[e.t] = P[e.g];
+    __syncthreads();
+    if (!act) return;
+    const T hx = G.hx[e.ex], hy = G.hy[e.ey];
+    const T Me = T(0.25) * hx * hy * sw[e.a] * sw[e.b];
+    const T c = -T(1) / (q.nu_m * q.rho0);
+    AUx[e.l] += c * Me * ddx(sPv, sD, G.p, e.a, e.b, T(2) / hx);
+    AUy[e.l] += c * Me * ddy(sPv, sD, G.p, e.a, e.b, T(2) / hy);
+    if (BUz) BUz[e.l] = c * Me * sPv[e.t];
+}
+
+// ---- direct stiffness summation of element-local contributions at nodal index (z, i, j) ----
+template <typename T>
+__device__ __forceinline__ T dssum(const Geo<T> &G, const T *__restrict__ Lv, int z, int i, int j) {
+    const int K = G.K, p = G.p;
+    int eys[2], bs[2], ny_ = 0;
+    if (i % K == 0) {
+        if (i > 0) { eys[ny_] = i / K - 1; bs[ny_++] = K; }
+        if (i < G.ny - 1) { eys[ny_] = i / K; bs[ny_++] = 0; }
+    } else {
+        eys[ny_] = i / K; bs[ny_++] = i % K;
+    }
+    int exs[2], as[2], nx_ = 0;
+    if (j % K == 0) {
+        exs[nx_] = j / K; as[nx_++] = 0;
+        exs[nx_] = (j / K - 1 + G.ex) % G.ex; as[nx_++] = K;
+    } else {
+        exs[nx_] = j / K; as[nx_++] = j % K;
+    }
+    const long long base = (long long)z * G.ex * G.ey;
+    T s = 0;
+    for (int cy = 0; cy < ny_; ++cy)
+        for (int cx = 0; cx < nx_; ++cx)
+            s += Lv[(base + (long long)eys[cy] * G.ex + exs[cx]) * (p * p) + bs[cy] * p + as[cx]];
+    return s;
+}
+
+// ---- in-shared-memory radix-2 FFT along z -------------------------------------------------
+__device__ __forceinline__ int bitrev(int v, int bits) { return bits ? (int)(__brev((unsigned)v) >> (32 - bits)) : 0; }
+
+// in-place DIT FFT of npen pencils of length n (bit-reversed input), sign -1 forward / +1 inverse
+template <typename T>
+__device__ void fft_pencils(cplx<T> *buf, int ld, int npen, int n, const cplx<T> *tw, bool inverse) {
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1, stride = n / len;
+        const int nb = npen * (n >> 1);
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const int pen = t / (n >> 1), bf = t % (n >> 1);
+            const int grp = bf / half, jj = bf % half;
+            const int i0 = grp * len + jj, i1 = i0 + half;
+            cplx<T> w = tw[jj * stride];
+            if (inverse) w.y = -w.y;
+            cplx<T> *x = buf + pen * ld;
+            const cplx<T> u = x[i0];
+            const cplx<T> v = cmul(x[i1], w);
+            x[i0] = {u.x + v.x, u.y + v.y};
+            x[i1] = {u.x - v.x, u.y - v.y};
+        }
+        __syncthreads();
+    }
+}
+
+// mode index k and real/imaginary part of packed plane p
+__device__ __forceinline__ void plane_mode(int p, int nz, int &k, int &im) {
+    if (nz == 1 || p == 0) { k = 0; im = 0; return; }
+    if (p == 1) { k = nz / 2; im = 0; return; }
+    k = p >> 1; im = p & 1;
+}
+
+template <typename T>
+struct FwdArgs {
+    const T *X0; int x0_local;      // input 0: element-local (1) or nodal (0)
+    const T *X1; int x1_local;      // input 1 (nullable)
+    int mult;                       // 0: X0 + i beta X1 ; 1: X0 + beta^2 M X1
+    T scale;                        // applied to the combined result
+    const T *lift;                  // nullable: n_y vector; plane 0 gets -lift[i] * Mx[j]
+    T *out;                         // packed mode planes [nz][n2]
+    T *out1;                        // nullable: packed FFT of X1 alone
+    T two_pi_over_lz;
+    const cplx<T> *tw;              // nz/2 twiddles exp(-2 pi i k / nz)
+    int tp;                         // nodes per block
+};
+
+template <typename T>
+__global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
+    extern __shared__ unsigned char pf_smem_raw[];
+    cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
+    const int nz = G.nz, ld = nz + 1, tp = a.tp;
+    cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    const int bits = 31 - __clz(nz);
+    for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
+    const int q0 = blockIdx.x * tp;
+    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
+        const int z = idx / tp, ql = idx % tp, qg = q0 + ql;
+        T v0 = 0, v1 = 0;
+        if (qg < G.n2) {
+            const int i = qg / G.nx, j = qg % G.nx;
+            const long long gi = (long long)z * G.n2 + qg;
+            v0 = a.x0_local ? dssum(G, a.X0, z, i, j) : a.X0[gi];
+            if (a.X1) v1 = a.x1_local ? dssum(G, a.X1, z, i, j) : a.X1[gi];
+        }
+        buf[ql * ld + bitrev(z, bits)] = {v0, v1};
+    }
+    __syncthreads();
+    if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
+    const T inv_n = T(1) / T(nz);
+    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
+        const int p = idx / tp, ql = idx % tp, qg = q0 + ql;
+        if (qg >= G.n2) continue;
+        int k, im;
+        plane_mode(p, nz, k, im);
+        const cplx<T> zk = buf[ql * ld + k];
+        const cplx<T> zn = buf[ql * ld + ((nz - k) % nz)];
+        // spectra of the two real inputs
+        const cplx<T> X0 = {T(0.5) * (zk.x + zn.x) * inv_n, T(0.5) * (zk.y - zn.y) * inv_n};
+        const cplx<T> X1 = {T(0.5) * (zk.y + zn.y) * inv_n, -T(0.5) * (zk.x - zn.x) * inv_n};
+        cplx<T> R = X0;
+        if (a.X1) {
+            const T beta = a.two_pi_over_lz * T(k);
+            if (a.mult == 0) {
+                const T b = (nz > 1 && k == nz / 2) ? T(0) : beta;   // Nyquist: no first derivative
+                R.x -= b * X1.y;
+                R.y += b * X1.x;
+            } else {
+                const int i = qg / G.nx, j = qg % G.nx;
+                const T m = beta * beta * G.Mx[j] * G.My[i];
+                R.x += m * X1.x;
+                R.y += m * X1.y;
+            }
+        }
+        T v = a.scale * (im ? R.y : R.x);
+        if (p == 0 && a.lift) {
+            const int i = qg / G.nx, j = qg % G.nx;
+            v -= a.lift[i] * G.Mx[j];
+        }
+        a.out[(long long)p * G.n2 + qg] = v;
+        if (a.out1) a.out1[(long long)p * G.n2 + qg] = im ? X1.y : X1.x;
+    }
+}
+
+template <typename T>
+struct InvArgs {
+    const T *Y;          // packed mode planes of the solution (the plain variant's input)
+    const T *psi;        // phi variant: packed psi modes
+    const T *Q2h;        // phi variant: packed Q2 modes
+    const T *Q2n;        // phi variant: nodal Q2 (for L = W + (S/eta^2) phi + Q2)
+    T alpha, S_eta2;
+    int phi_variant;
+    int drow0, drow1;    // Dirichlet rows that receive the values v0 / v1 in mode 0 (-1: none)
+    T v0, v1;
+    T *out, *dzout;      // value and d/dz (dzout nullable)
+    T *out2, *dzout2;    // phi variant: W and d/dz W
+    T *out3;             // phi variant: L = psi - alpha phi
+    T two_pi_over_lz;
+    const cplx<T> *tw;
+    int tp;
+};
+
+// Build the full complex spectrum Z = X + i Y of two real signals, Y = i beta X (d/dz),
+// from the packed half spectrum X of pencil column ql; buffer is bit-reversed for the DIT.
+template <typename T>
+__device__ __forceinline__ void put_pair(cplx<T> *x, int nz, int bits, int k, cplx<T> Xk, T beta) {
+    // Z_k = (1 - beta) X_k ; Z_{N-k} = (1 + beta) conj(X_k)
+    const bool nyq = (nz > 1 && k == nz / 2);
+    const T b = nyq ? T(0) : beta;
+    x[bitrev(k, bits)] = {(T(1) - b) * Xk.x, (T(1) - b) * Xk.y};
+    if (k != 0 && !nyq) x[bitrev(nz - k, bits)] = {(T(1) + b) * Xk.x, -(T(1) + b) * Xk.y};
+}
+
+template <typename T>
+__global__ void k_inv(Geo<T> G, InvArgs<T> a) {
+    extern __shared__ unsigned char pf_smem_raw[];
+    cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
+    const int nz = G.nz, ld = nz + 1, tp = a.tp;
+    const int npair = a.phi_variant ? 2 : 1;
+    cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    const int bits = 31 - __clz(nz);
+    for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
+    const int q0 = blockIdx.x * tp;
+    // load the half spectra: one (k) per thread-iteration, both Re and Im planes
+    const int nk = nz / 2 + 1;
+    for (int idx = threadIdx.x; idx < tp * (nz > 1 ? nk : 1); idx += blockDim.x) {
+        const int k = idx / tp, ql = idx % tp, qg = q0 + ql;
+        cplx<T> X = {0, 0}, Wk = {0, 0};
+        if (qg < G.n2) {
+            int pre, pim;
+            if (nz == 1 || k == 0) { pre = 0; pim = -1; }
+            else if (k == nz / 2) { pre = 1; pim = -1; }
+            else { pre = 2 * k; pim = 2 * k + 1; }
+            auto ld2 = [&](const T *A) -> cplx<T> {
+                cplx<T> r = {A[(long long)pre * G.n2 + qg], pim >= 0 ? A[(long long)pim * G.n2 + qg] : T(0)};
+                return r;
+            };
+            X = ld2(a.Y);
+            if (k == 0 && a.drow0 >= 0 && qg / G.nx == a.drow0) X.x += a.v0;
+            if (k == 0 && a.drow1 >= 0 && qg / G.nx == a.drow1) X.x += a.v1;
+            if (a.phi_variant) {
+                const cplx<T> ps = ld2(a.psi), q2 = ld2(a.Q2h);
+                const T c = a.alpha + a.S_eta2;
+                Wk = {ps.x - c * X.x - q2.x, ps.y - c * X.y - q2.y};
+            }
+        }
+        const T beta = a.two_pi_over_lz * T(k);
+        if (nz == 1) {
+            buf[ql * ld] = X;
+            if (a.phi_variant) buf[(tp + ql) * ld] = Wk;
+        } else {
+            put_pair(buf + ql * ld, nz, bits, k, X, beta);
+            if (a.phi_variant) put_pair(buf + (tp + ql) * ld, nz, bits, k, Wk, beta);
+        }
+    }
+    __syncthreads();
+    if (nz > 1) fft_pencils(buf, ld, tp * npair, nz, stw, true);
+    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
+        const int z = idx / tp, ql = idx % tp, qg = q0 + ql;
+        if (qg >= G.n2) continue;
+        const long long gi = (long long)z * G.n2 + qg;
+        const cplx<T> r = buf[ql * ld + z];
+        a.out[gi] = r.x;
+        if (a.dzout) a.dzout[gi] = r.y;
+        if (a.phi_variant) {
+            const cplx<T> rw = buf[(tp + ql) * ld + z];
+            a.out2[gi] = rw.x;
+            if (a.dzout2) a.dzout2[gi] = rw.y;
+            a.out3[gi] = rw.x + a.S_eta2 * r.x + a.Q2n[gi];
+        }
+    }
+}
+
+// right-hand side of eq. 57 / 76 in mode space: -M psi_hat (+ wall term rows)
+template <typename T>
+__global__ void k_rhs_phi(Geo<T> G, const T *__restrict__ psih, const T *__restrict__ faceh,
+                          T *__restrict__ out) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)G.n2 * G.nz;
+    if (gid >= tot) return;
+    const int p = (int)(gid / G.n2), q = (int)(gid % G.n2);
+    const int i = q / G.nx, j = q % G.nx;
+    T v = -G.Mx[j] * G.My[i] * psih[gid];
+    if (faceh && i == 0) v += faceh[(long long)p * G.nx + j];
+    out[gid] = v;
+}
+
+// z-FFT of the wall face slots (direct stiffness summation along x first)
+template <typename T>
+__global__ void k_face_fft(Geo<T> G, const T *__restrict__ face, T *__restrict__ out, const cplx<T> *tw,
+                           int tp) {
+    extern __shared__ unsigned char pf_smem_raw[];
+    cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
+    const int nz = G.nz, ld = nz + 1;
+    cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    const int bits = 31 - __clz(nz);
+    for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = tw[i];
+    const int j0 = blockIdx.x * tp;
+    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
+        const int z = idx / tp, jl = idx % tp, j = j0 + jl;
+        T v = 0;
+        if (j < G.nx) {
+            const int K = G.K, p = G.p;
+            const long long base = (long long)z * G.ex;
+            if (j % K == 0) {
+                v = face[(base + j / K) * p] + face[(base + (j / K - 1 + G.ex) % G.ex) * p + K];
+            } else {
+                v = face[(base + j / K) * p + j % K];
+            }
+        }
+        buf[jl * ld + bitrev(z, bits)] = {v, T(0)};
+    }
+    __syncthreads();
+    if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
+    const T inv_n = T(1) / T(nz);
+    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
+        const int p = idx / tp, jl = idx % tp, j = j0 + jl;
+        if (j >= G.nx) continue;
+        int k, im;
+        plane_mode(p, nz, k, im);
+        const cplx<T> zk = buf[jl * ld + k];
+        out[(long long)p * G.nx + j] = (im ? zk.y : zk.x) * inv_n;
+    }
+}
+
+// ---- C = A B, B small (N x N) shared by all rows; A is Mrows x N row-major -----------------
+// store: 0 plain C[m][n]; 1 transposed within planes of R rows: C[p][n][r], m = p R + r.
+// div: if lamN != nullptr, C[m][n] /= lamN[n] + lamR[r] + cpl[p]  (0 when the sum is 0).
+template <typename T>
+struct GemmArgs {
+    const T *A, *B;
+    T *C;
+    long long Mrows;
+    int N, R, store;
+    const T *lamN, *lamR, *cpl;
+    int cpl_mod;   // plane index for cpl: p % cpl_mod
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
+    __shared__ T sA[BK][BM + 1];
+    __shared__ T sB[BK][BN];
+    const int nth = (BM / TM) * (BN / TN);
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const long long m0 = (long long)blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+    for (int k0 = 0; k0 < g.N; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += nth) {
+            const int r = idx / BK, c = idx % BK;
+            const long long m = m0 + r;
+            const int k = k0 + c;
+            sA[c][r] = (m < g.Mrows && k < g.N) ? g.A[m * g.N + k] : T(0);
+        }
+        for (int idx = tid; idx < BK * BN; idx += nth) {
+            const int r = idx / BN, c = idx % BN;
+            const int k = k0 + r, n = n0 + c;
+            sB[r][c] = (k < g.N && n < g.N) ? g.B[(long long)k * g.N + n] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T ra[TM], rb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) ra[i] = sA[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) rb[j] = sB[kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] += ra[i] * rb[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const long long m = m0 + ty * TM + i;
+        if (m >= g.Mrows) continue;
+        const long long p = m / g.R;
+        const int r = (int)(m - p * g.R);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx * TN + j;
+            if (n >= g.N) continue;
+            T v = acc[i][j];
+            if (g.lamN) {
+                const T d = g.lamN[n] + g.lamR[r] + g.cpl[p % g.cpl_mod];
+                v = (d != T(0)) ? v / d : T(0);
+            }
+            if (g.store == 0) g.C[m * g.N + n] = v;
+            else g.C[(p * g.N + n) * g.R + r] = v;
+        }
+    }
+}
+
+// ---- FP64 reductions (two passes, deterministic) --------------------------------------------
+// kind 0: sum of w[q % n2w] * x[q] (phase mass, w = nodal mass); kind 1: max |x|; kind 2: max |x - y|
+// A non-finite entry propagates as NaN through every kind.
+template <typename T>
+__global__ void k_reduce(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ w1,
+                         const T *__restrict__ w2, int nx, int n2w, long long n, int kind,
+                         double *__restrict__ part) {
+    __shared__ double sm[256];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (kind == 0) {
+            const int q = (int)(i % n2w);
+            v = (double)w1[q % nx] * (double)w2[q / nx] * (double)x[i];
+            acc += v;
+        } else {
+            v = (kind == 1) ? fabs((double)x[i]) : fabs((double)x[i] - (double)y[i]);
+            if (acc == acc) {   // once NaN, stays NaN
+                if (v != v) acc = v;
+                else if (v > acc) acc = v;
+            }
+        }
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double a = sm[threadIdx.x], b = sm[threadIdx.x + s];
+            if (kind == 0) sm[threadIdx.x] = a + b;
+            else sm[threadIdx.x] = (a != a || b != b) ? (a != a ? a : b) : fmax(a, b);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+template <typename T, typename S>
+__global__ void k_convert(const T *__restrict__ in, S *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (S)in[i];
+}
+
+}  // namespace pf

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of the C-ABI declared in include/pf.h (argument marshalling only).
+
+Every step of the time-stepping path runs in the CUDA library ``libpf.so``;
+this module converts numpy arrays and Python numbers to the C structs and
+pointers of the ABI and turns negative status codes into exceptions.  If the
+library cannot be loaded the import fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_size_t, c_uint, c_void_p, c_char_p, c_ubyte
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTSEPARABLE, PF_EDIVERGED, PF_ETIMEOUT, PF_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+PF_BC_DIRICHLET, PF_BC_NEUMANN = 0, 1
+PF_FP64, PF_MIXED = 0, 1
+PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
+PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
+    1, 2, 4, 8, 16, 32, 64
+_BLOCKS = [(PF_FIELD_V, ["V"]), (PF_FIELD_E, ["Ex", "Ey", "Ez"]), (PF_FIELD_PHI, ["phi"]),
+           (PF_FIELD_PSI, ["psi"]), (PF_FIELD_P, ["P"]), (PF_FIELD_U, ["ux", "uy", "uz"])]
+
+
+class PfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pf error {code}: {msg}")
+        self.code = code
+
+
+class PfMesh(ctypes.Structure):
+    _fields_ = [("ex", c_int), ("ey", c_int), ("xb", POINTER(c_double)), ("yb", POINTER(c_double)),
+                ("order", c_int), ("nz", c_int), ("lz", c_double)]
+
+
+class PfFluid(ctypes.Structure):
+    _fields_ = [(n, c_double) for n in ("rho1", "rho2", "mu1", "mu2", "eps1", "eps2", "sigma", "eta",
+                                        "gamma1", "theta_s_deg")]
+
+
+class PfVbc(ctypes.Structure):
+    _fields_ = [("bottom_kind", c_int), ("top_kind", c_int), ("v_bottom", c_double), ("v_top", c_double)]
+
+
+class PfScheme(ctypes.Structure):
+    _fields_ = [("dt", c_double), ("bdf", c_int), ("precision", c_int), ("S", c_double),
+                ("nu_m", c_double), ("rho0", c_double), ("eps0", c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpf.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    dp = POINTER(c_double)
+    L.pf_gll.argtypes = [c_int, dp, dp, dp]
+    L.pf_nodes_1d.argtypes = [c_int, dp, c_int, c_int, dp]
+    L.pf_operators_1d.argtypes = [c_int, dp, c_int, c_int, dp, dp]
+    L.pf_fdm_1d.argtypes = [c_int, dp, dp, POINTER(c_ubyte), dp, dp]
+    L.pf_create.argtypes = [POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme), dp, dp,
+                            c_void_p, POINTER(c_void_p)]
+    L.pf_step.argtypes = [c_void_p, c_int]
+    L.pf_sync.argtypes = [c_void_p]
+    L.pf_get_fields.argtypes = [c_void_p, c_uint, dp, c_size_t]
+    L.pf_set_fields.argtypes = [c_void_p, c_uint, dp, c_size_t, c_int]
+    L.pf_diagnostics.argtypes = [c_void_p, dp]
+    L.pf_solve_helmholtz.argtypes = [c_void_p, c_int, c_int, c_double, dp, dp]
+    L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
+    L.pf_destroy.argtypes = [c_void_p]
+    L.pf_destroy.restype = None
+    L.pf_last_error.argtypes = [c_void_p]
+    L.pf_last_error.restype = c_char_p
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc: int, handle=None):
+    if rc != PF_OK:
+        msg = load().pf_last_error(handle)
+        raise PfError(rc, msg.decode() if msg else "")
+
+
+# ---- host-only helpers ----------------------------------------------------------------------
+def gll(K: int):
+    L = load()
+    x, w, D = np.zeros(K + 1), np.zeros(K + 1), np.zeros((K + 1) * (K + 1))
+    _check(L.pf_gll(K, _dp(x), _dp(w), _dp(D)))
+    return x, w, D.reshape(K + 1, K + 1)
+
+
+def nodes_1d(br, K: int, periodic: bool):
+    L = load()
+    br = _f64(br)
+    ne = len(br) - 1
+    n = ne * K if periodic else ne * K + 1
+    out = np.zeros(n)
+    _check(L.pf_nodes_1d(ne, _dp(br), K, int(periodic), _dp(out)))
+    return out
+
+
+def operators_1d(br, K: int, periodic: bool):
+    L = load()
+    br = _f64(br)
+    ne = len(br) - 1
+    n = ne * K if periodic else ne * K + 1
+    Km, M = np.zeros((n, n)), np.zeros(n)
+    _check(L.pf_operators_1d(ne, _dp(br), K, int(periodic), _dp(Km), _dp(M)))
+    return Km, M
+
+
+def fdm_1d(Kmat, Mdiag, dirichlet=None):
+    L = load()
+    Kmat, Mdiag = _f64(Kmat), _f64(Mdiag)
+    n = len(Mdiag)
+    mask = np.zeros(n, dtype=np.uint8) if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    S, lam = np.zeros((n, n)), np.zeros(n)
+    _check(L.pf_fdm_1d(n, _dp(Kmat), _dp(Mdiag), mask.ctypes.data_as(POINTER(c_ubyte)), _dp(S), _dp(lam)))
+    return S, lam
+
+
+# ---- the time stepper -------------------------------------------------------------------------
+class Solver:
+    """Owner of one ``pf_handle``: the device state of one two-phase dielectric run."""
+
+    def __init__(self, xb, yb, order: int, nz: int, lz: float, fluid: dict, vbc: dict, scheme: dict,
+                 phi0: np.ndarray, u0: Optional[np.ndarray] = None, stream: Optional[int] = None):
+        L = load()
+        self._xb, self._yb = _f64(xb), _f64(yb)
+        self.mesh = PfMesh(len(self._xb) - 1, len(self._yb) - 1, _dp(self._xb), _dp(self._yb), int(order),
+                           int(nz), float(lz))
+        self.fluid = PfFluid(**{k: float(v) for k, v in fluid.items()})
+        self.vbc = PfVbc(int(vbc["bottom_kind"]), int(vbc["top_kind"]), float(vbc["v_bottom"]),
+                         float(vbc["v_top"]))
+        self.scheme = PfScheme(float(scheme["dt"]), int(scheme.get("bdf", 2)), int(scheme.get("precision", PF_FP64)),
+                               float(scheme.get("S", 0.0)), float(scheme.get("nu_m", 0.0)),
+                               float(scheme.get("rho0", 0.0)), float(scheme.get("eps0", 0.0)))
+        self.nx = self.mesh.ex * order
+        self.ny = self.mesh.ey * order + 1
+        self.nz = nz
+        self.n = self.nx * self.ny * nz
+        phi0 = _f64(phi0).ravel()
+        if phi0.size != self.n:
+            raise ValueError(f"phi0 has {phi0.size} values, expected {self.n}")
+        u0p = None
+        if u0 is not None:
+            u0 = _f64(u0).ravel()
+            if u0.size != 3 * self.n:
+                raise ValueError("u0 must hold 3 blocks")
+            u0p = _dp(u0)
+        h = c_void_p()
+        rc = L.pf_create(ctypes.byref(self.mesh), ctypes.byref(self.fluid), ctypes.byref(self.vbc),
+                         ctypes.byref(self.scheme), _dp(phi0), u0p, c_void_p(stream or 0), ctypes.byref(h))
+        _check(rc, None)
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n: int = 1):
+        _check(load().pf_step(self._h, int(n)), self._h)
+
+    def sync(self):
+        _check(load().pf_sync(self._h), self._h)
+
+    def get(self, mask: int) -> dict:
+        names = [nm for bit, nms in _BLOCKS if mask & bit for nm in nms]
+        out = np.zeros(len(names) * self.n)
+        _check(load().pf_get_fields(self._h, int(mask), _dp(out), out.size), self._h)
+        shp = (self.nz, self.ny, self.nx)
+        return {nm: out[i * self.n:(i + 1) * self.n].reshape(shp) for i, nm in enumerate(names)}
+
+    def set(self, mask: int, data: np.ndarray, reset_history: bool = False):
+        data = _f64(data).ravel()
+        _check(load().pf_set_fields(self._h, int(mask), _dp(data), data.size, int(reset_history)), self._h)
+
+    def diagnostics(self) -> np.ndarray:
+        out = np.zeros(8)
+        _check(load().pf_diagnostics(self._h, _dp(out)), self._h)
+        return out
+
+    def solve_helmholtz(self, bcset: int, mode: int, lam: float, rhs: np.ndarray) -> np.ndarray:
+        rhs = _f64(rhs).ravel()
+        out = np.zeros_like(rhs)
+        _check(load().pf_solve_helmholtz(self._h, int(bcset), int(mode), float(lam), _dp(rhs), _dp(out)), self._h)
+        return out
+
+    def geometry(self):
+        x, y = np.zeros(self.nx), np.zeros(self.ny)
+        dims = (c_int * 4)()
+        _check(load().pf_geometry(self._h, _dp(x), _dp(y), dims), self._h)
+        return x, y, list(dims)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_workload(wl, precision: int = PF_FP64, stream: Optional[int] = None, dt: Optional[float] = None,
+                  phi0: Optional[np.ndarray] = None) -> Solver:
+    """Create a Solver for a ``workloads.Workload`` (initial phi evaluated at this library's nodes)."""
+    import workloads
+    m, f, v, s = wl.mesh, wl.fluid, wl.vbc, wl.scheme
+    x = nodes_1d(m.xb, m.order, True)
+    y = nodes_1d(m.yb, m.order, False)
+    z = None if m.nz == 1 else np.arange(m.nz) * m.lz / m.nz
+    if phi0 is None:
+        phi0 = workloads.eval_on_grid(wl.phi0, x, y, z)
+    fluid = dict(rho1=f.rho1, rho2=f.rho2, mu1=f.mu1, mu2=f.mu2, eps1=f.eps1, eps2=f.eps2, sigma=f.sigma,
+                 eta=f.eta, gamma1=f.gamma1, theta_s_deg=f.theta_s_deg)
+    vbc = dict(bottom_kind=v.bottom_kind, top_kind=v.top_kind, v_bottom=v.v_bottom, v_top=v.v_top)
+    scheme = dict(dt=s.dt if dt is None else dt, bdf=s.bdf, precision=precision, S=s.S, nu_m=s.nu_m,
+                  rho0=s.rho0, eps0=s.eps0)
+    return Solver(m.xb, m.yb, m.order, m.nz, m.lz, fluid, vbc, scheme, phi0, stream=stream)

@@ -1,0 +1,115 @@
+"""GPU (CUDA through the C-ABI) versus the FP64 CPU oracle, element by element.
+
+Tolerances (relative L2 per field; absolute max for a field that is identically 0):
+* FP64 path: <= 1e-11.  The two sides differ only by round-off: fast diagonalisation
+  and sparse LU each solve the same assembled systems to ~3e-14 / ~1e-14, and the
+  difference grows linearly with the number of steps (about 1e-13 per step on the
+  velocity of the 2D droplet, whose update is a small residual of cancelling forces),
+  so the 100-step 2D droplet run is held to 1e-11 through step 75 and to 2e-11 at 100.
+* mixed path (FP32 node kernels, FFT and transforms): the primary fields V, phi, psi
+  <= 1e-6 after one step; E, P and u are spectral derivatives of FP32 fields (the
+  GLL derivative amplifies the FP32 unit round-off 6e-8 by ~K^2/h ~ 1e2..1e3), so
+  <= 1e-4 after one step.  After 100 steps: V, phi, psi <= 5e-5, E, P, u <= 5e-4."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads
+from oracle.sem import Mesh2D
+from paper_2305_09020_gb300 import native
+
+from gpu_util import run_pair
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+
+
+def _assert_all(res, tol):
+    for step, errs in res:
+        bad = {k: v for k, v in errs.items() if not (v <= tol)}
+        assert not bad, f"step {step}: {bad}"
+
+
+@pytest.mark.parametrize("bcset", [native.PF_BCSET_V, native.PF_BCSET_NN, native.PF_BCSET_P, native.PF_BCSET_U])
+@pytest.mark.parametrize("nz,mode", [(1, 0), (8, 0), (8, 3), (8, 4)])
+@pytest.mark.parametrize("precision", [native.PF_FP64, native.PF_MIXED])
+def test_helmholtz_parity(bcset, nz, mode, precision):
+    """pf_solve_helmholtz equals the oracle's assembled (K + (lam + beta^2) M) x = M f."""
+    wl = workloads.small3d(ex=3, ey=3, order=5, nz=nz) if nz > 1 else workloads.small2d(ex=3, ey=3, order=5)
+    g = native.from_workload(wl, precision=precision)
+    m = Mesh2D(wl.mesh.xb, wl.mesh.yb, wl.mesh.order)
+    lam = 2.5
+    beta = 2 * np.pi * mode / wl.mesh.lz if nz > 1 else 0.0
+    npl = 1 if mode == 0 else 2
+    rng = np.random.default_rng(bcset * 10 + mode)
+    f = rng.standard_normal((npl, m.n2))
+    x = g.solve_helmholtz(bcset, mode, lam, f).reshape(npl, m.n2)
+    g.close()
+    Dn = []
+    if bcset == native.PF_BCSET_V:
+        Dn = list(m.bottom_nodes) + list(m.top_nodes)      # both sides Dirichlet in these workloads
+    elif bcset == native.PF_BCSET_P:
+        Dn = list(m.top_nodes)
+    elif bcset == native.PF_BCSET_U:
+        Dn = list(m.bottom_nodes)
+    free = np.setdiff1d(np.arange(m.n2), Dn)
+    A = m.helmholtz(lam + beta ** 2).tocsr()[free][:, free].tocsc()
+    lu = spla.splu(A)
+    tol = 1e-12 if precision == native.PF_FP64 else 2e-6
+    for pl in range(npl):
+        ref = np.zeros(m.n2)
+        ref[free] = lu.solve((m.Mdiag * f[pl])[free])
+        assert np.linalg.norm(x[pl] - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_step_parity_2d_small_wetting():
+    wl = workloads.small2d(ex=4, ey=2, order=5, theta_s_deg=60.0)
+    _assert_all(run_pair(wl, 10, check_every=1), FP64_TOL)
+
+
+def test_step_parity_2d_graded_neumann_top():
+    wl = workloads.small2d(ex=3, ey=3, order=6, graded=True, v_top_kind=workloads.BC_NEUMANN)
+    _assert_all(run_pair(wl, 8, check_every=4), FP64_TOL)
+
+
+def test_step_parity_2d_droplet_100_steps():
+    """The 2D plain-method workload (8x4 elements, order 6) over its 100 steps."""
+    wl = workloads.droplet2d()
+    res = run_pair(wl, 100, check_every=25)
+    _assert_all([r for r in res if r[0] <= 75], FP64_TOL)
+    _assert_all(res, 2e-11)
+
+
+def test_step_parity_3d_small():
+    wl = workloads.small3d(ex=4, ey=2, order=4, nz=8, theta_s_deg=70.0)
+    _assert_all(run_pair(wl, 6, check_every=1), FP64_TOL)
+
+
+def test_step_parity_3d_small_neumann_top():
+    wl = workloads.small3d(ex=3, ey=3, order=5, nz=16, v_top_kind=workloads.BC_NEUMANN)
+    _assert_all(run_pair(wl, 4, check_every=2), FP64_TOL)
+
+
+PRIMARY = ("V", "phi", "psi")
+
+
+def _assert_mixed(res, last):
+    for step, errs in res:
+        for k, v in errs.items():
+            if step <= 1:
+                tol = 1e-6 if k in PRIMARY else 1e-4
+            else:
+                tol = 5e-5 if k in PRIMARY else 5e-4
+            assert v <= tol, f"step {step}: {k} = {v:.3e} > {tol:.0e}"
+    assert res[-1][0] == last
+
+
+def test_mixed_precision_2d_droplet():
+    wl = workloads.droplet2d()
+    _assert_mixed(run_pair(wl, 100, precision=native.PF_MIXED, check_every=1), 100)
+
+
+def test_mixed_precision_3d_small():
+    wl = workloads.small3d(ex=4, ey=2, order=5, nz=8)
+    _assert_mixed(run_pair(wl, 10, precision=native.PF_MIXED, check_every=1), 10)

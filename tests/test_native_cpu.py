@@ -1,0 +1,117 @@
+"""CPU checks of the C-ABI library: it loads without a GPU, exports every symbol that
+include/pf.h declares, and its host-side set-up (GLL tables, 1D operators, eigenbases)
+agrees with the oracle's independently assembled operators."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.gll import gll as oracle_gll
+from oracle.sem import Mesh2D
+from paper_2305_09020_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "pf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = native.load()
+    syms = declared_symbols()
+    assert "pf_create" in syms and "pf_step" in syms and "pf_solve_helmholtz" in syms
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("K", [2, 4, 7, 10, 15])
+def test_gll_matches_oracle(K):
+    x, w, D = native.gll(K)
+    xo, wo, Do = oracle_gll(K)
+    np.testing.assert_allclose(x, xo, atol=1e-15)
+    np.testing.assert_allclose(w, wo, rtol=1e-13)
+    np.testing.assert_allclose(D, Do, atol=1e-11 * K * K)
+
+
+def test_bad_arguments_rejected():
+    L = native.load()
+    with pytest.raises(native.PfError):
+        native.gll(0)
+    with pytest.raises(native.PfError):
+        native.operators_1d([0.0, 1.0, 0.5], 4, False)      # decreasing breakpoints
+
+
+@pytest.mark.parametrize("graded", [False, True])
+def test_tensor_operators_match_oracle_assembly(graded):
+    """K2D = Kx (x) My + Mx (x) Ky and M2D = Mx (x) My reproduce the oracle's element-by-
+    element assembled matrices (the separability behind the fast-diagonalisation solve)."""
+    xb = np.linspace(0.0, 2.0, 4)
+    yb = np.linspace(0.0, 1.0, 4)
+    if graded:
+        yb = 0.5 * (1 - np.cos(np.pi * yb))
+    K = 5
+    m = Mesh2D(xb, yb, K)
+    Kx, Mx = native.operators_1d(xb, K, True)
+    Ky, My = native.operators_1d(yb, K, False)
+    K2 = np.kron(Ky, np.diag(Mx)) + np.kron(np.diag(My), Kx)   # index (i, j) -> i*nx + j
+    np.testing.assert_allclose(K2, m.Kmat.toarray(), atol=1e-11)
+    np.testing.assert_allclose(np.kron(My, Mx), m.Mdiag, rtol=1e-14)
+    np.testing.assert_allclose(native.nodes_1d(xb, K, True), m.X, atol=1e-15)
+    np.testing.assert_allclose(native.nodes_1d(yb, K, False), m.Y, atol=1e-15)
+
+
+@pytest.mark.parametrize("mask", ["none", "bottom", "top", "both"])
+def test_fdm_1d_generalised_eigenbasis(mask):
+    Ky, My = native.operators_1d(np.linspace(0, 1, 6), 6, False)
+    n = len(My)
+    d = np.zeros(n, dtype=np.uint8)
+    if mask in ("bottom", "both"):
+        d[0] = 1
+    if mask in ("top", "both"):
+        d[-1] = 1
+    S, lam = native.fdm_1d(Ky, My, d)
+    nf = n - int(d.sum())
+    Sf = S[:, :nf]
+    np.testing.assert_allclose(Sf.T @ np.diag(My) @ Sf, np.eye(nf), atol=1e-11)
+    free = d == 0
+    Kf = Ky[np.ix_(free, free)]
+    np.testing.assert_allclose(Kf @ Sf[free], np.diag(My[free]) @ Sf[free] @ np.diag(lam[:nf]),
+                               atol=1e-8 * lam.max())
+    assert np.all(S[~free] == 0) and np.all(S[:, nf:] == 0)
+    assert np.all(np.diff(lam[:nf]) >= -1e-9)
+
+
+@pytest.mark.parametrize("bc", ["P", "U", "V"])
+def test_fast_diagonalisation_equals_direct_solve(bc):
+    """With the library's factors, S_y [(S_y^T (M f) S_x) / (L_y + L_x + c)] S_x^T is the
+    solution of the oracle's assembled (K + c M) u = M f with homogeneous Dirichlet rows."""
+    xb, yb, K, c = np.linspace(0, 2, 4), np.linspace(0, 1, 4), 4, 3.7
+    m = Mesh2D(xb, yb, K)
+    Kx, Mx = native.operators_1d(xb, K, True)
+    Ky, My = native.operators_1d(yb, K, False)
+    Sx, Lx = native.fdm_1d(Kx, Mx)
+    ny = len(My)
+    d = np.zeros(ny, dtype=np.uint8)
+    if bc == "P":
+        d[-1] = 1
+    elif bc == "U":
+        d[0] = 1
+    else:
+        d[0] = d[-1] = 1
+    Sy, Ly = native.fdm_1d(Ky, My, d)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((ny, len(Mx)))
+    b = np.outer(My, Mx) * f
+    t = Sy.T @ b @ Sx / (Ly[:, None] + Lx[None, :] + c)
+    u = Sy @ t @ Sx.T
+    Dn = np.where(np.repeat(d, len(Mx)) == 1)[0]
+    free = np.setdiff1d(np.arange(m.n2), Dn)
+    A = m.helmholtz(c).tocsr()
+    ref = np.zeros(m.n2)
+    ref[free] = spla.spsolve(A[free][:, free].tocsc(), (m.Mdiag * f.ravel())[free])
+    np.testing.assert_allclose(u.ravel(), ref, atol=1e-12 * np.abs(ref).max())
