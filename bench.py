@@ -1,0 +1,278 @@
+#!/usr/bin/env python
+"""Throughput of the per-time-step path (Algorithm 2) on the 3D hybrid droplet workload.
+
+Workload (default): 16x8 spectral elements of order 8 times Nz = 64 Fourier planes,
+sphere of radius 0.25 on the bottom electrode (eps ratio 10, rho ratio 2, mu ratio 5),
+V = 2 / 0, dt = 5e-5.  One "step" = one full time step (V, E, psi, phi, P, u), all of it
+in the CUDA library through the C-ABI.  Metric: DOF-steps/s, DOF = real values of one
+scalar field = n_x n_y Nz = 532,480.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-steps/s at stated err vs FP64 oracle; time-to-equilibrium warm vs cold"
+UNIT = "DOF-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2        # FP64 rate of GB300 (about 1.25 TFLOP/s at 2.07 GHz)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---- CPU oracle sample (cpu_baseline and --impl reference) -----------------------------------
+def oracle_sample(nsteps: int, warmup: int):
+    """Steady-state BDF2 steps of the FP64 oracle on the workload's element mesh and physics
+    with Nz = 8 planes (the oracle's sparse LU factorisations per mode make the full Nz = 64
+    case take minutes per step).  Returns (DOF-steps/s, seconds, description)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import workloads
+    from oracle.runner import solver_of
+    wl = workloads.droplet3d()
+    wl.mesh.nz = 8
+    sol = solver_of(wl, init=False)
+    Zg, Yg, Xg = np.meshgrid(sol.zc, sol.mesh.Y, sol.mesh.X, indexing="ij")
+    sol.set_initial(wl.phi0(Xg, Yg, Zg).reshape(sol.nz, sol.mesh.n2), max_iter=3)
+    for _ in range(max(2, warmup)):       # BDF1 + first BDF2 step build the LU factors
+        sol.step()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        sol.step()
+    dt = time.perf_counter() - t0
+    dof = sol.mesh.n2 * sol.nz
+    desc = (f"oracle (scipy SuperLU, numpy FFT), droplet3d element mesh 16x8 P=8 with Nz=8 planes "
+            f"({dof} DOF), {nsteps} steady BDF2 step(s) after {max(2, warmup)} warm-up steps; "
+            f"initial-potential iterations capped at 3 (set-up is not timed)")
+    return dof * nsteps / dt, dt, desc
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    val, secs, desc = oracle_sample(steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "droplet3d (oracle sample: Nz=8)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- clocks ------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if not sm:
+            return None
+        mx = max(float(r[2]) for r in rows if len(r) >= 9)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) >= 9 and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": reasons, "samples": len(sm)}
+
+
+# ---- algorithmic work per kernel class ----------------------------------------------------------
+def fdm_flops_per_step(nx, ny, nz, d3):
+    """Fast-diagonalisation flops of one step: 4 n2 (n_x + n_y) per real plane and solve
+    (two GEMM passes each way); planes: V, psi, phi, P (Nz each) and d velocity components."""
+    n2 = nx * ny
+    planes = nz * (4 + (3 if d3 else 2))
+    return 4.0 * n2 * (nx + ny) * planes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import workloads
+    from paper_2305_09020_gb300 import native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prec = native.PF_MIXED if args.precision == "mixed" else native.PF_FP64
+    wl = workloads.droplet3d()
+    m = wl.mesh
+    nx, ny, nz = m.ex * m.order, m.ey * m.order + 1, m.nz
+    dof = nx * ny * nz
+    h = native.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    h.step(args.warmup)
+    barrier()
+    launches0 = h.profile_read()
+    clk = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.cudart().cudaProfilerStart()    # profilers started with --profile-from-start off see only this
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)               # L2 flush between timed steps (not timed)
+        ev[k][0].record(stream)
+        h.step(1)
+        ev[k][1].record(stream)
+    barrier()
+    torch.cuda.cudart().cudaProfilerStop()
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches1 = h.profile_read()
+    gpu_launches = sum(launches1[k][1] - launches0[k][1] for k in launches1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = dof * args.steps * world / (ms * 1e-3)
+
+    extras = {}
+    if not args.skip_extras:
+        # per-class device time of the same step, CUDA events on the library's stream
+        h.profile(True)
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            h.step(1)
+        cls = h.profile_read()
+        h.profile(False)
+        tot = sum(v[0] for v in cls.values())
+        top = max(cls, key=lambda k: cls[k][0])
+        pk, src = peaks()
+        per_launch_ms = cls[top][0] / max(1, cls[top][1] - launches1[top][1])
+        roof = None
+        if top == "gemm":
+            flops = fdm_flops_per_step(nx, ny, nz, nz > 1) * args.steps
+            nlaunch = cls["gemm"][1] - launches1["gemm"][1]
+            achieved = flops / nlaunch / (per_launch_ms * 1e-3) / 1e12
+            if prec == native.PF_MIXED:
+                peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            else:
+                peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "k_gemm (fast-diagonalisation transforms)", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {'128 FP32 FMA' if prec == native.PF_MIXED else '2 FP64 FMA'}"
+                                   f"/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+        else:
+            roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": None, "traffic": None, "peak_source": src}
+        extras["roofline"] = roof
+        extras["kernel_share"] = {k: round(v[0] / tot, 4) for k, v in cls.items() if v[0] > 0}
+
+        # end to end through the C-ABI with host buffers: set phi, u from pinned host memory,
+        # step, read V, phi, P, u back into pinned host memory
+        n_e2e = min(args.steps, 20)
+        hin = torch.empty(4 * dof, dtype=torch.float64, pin_memory=True).numpy()
+        hout = torch.empty(6 * dof, dtype=torch.float64, pin_memory=True).numpy()
+        mask_in = native.PF_FIELD_PHI | native.PF_FIELD_U
+        mask_out = native.PF_FIELD_V | native.PF_FIELD_PHI | native.PF_FIELD_P | native.PF_FIELD_U
+        h.get_into(mask_in, hin)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            h.set(mask_in, hin)
+            h.step(1)
+            h.get_into(mask_out, hout)
+            hin[:dof] = hout[dof:2 * dof]          # phi
+            hin[dof:] = hout[3 * dof:]             # u
+        barrier()
+        te = time.perf_counter() - t0
+        extras["e2e"] = {"value": dof * n_e2e * world / te, "unit": UNIT,
+                         "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes),
+                         "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,phi,P,u), pinned host buffers"}
+        if rank == 0 and world == 1:
+            val, secs, desc = oracle_sample(1, 2)
+            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    h.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == native.PF_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": "droplet3d: 16x8 elements order 8 x Nz=64 planes, sphere r=0.25 on the "
+                                   "electrode, eps/rho/mu ratios 10/2/5, V=2, dt=5e-5",
+                       "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": gpu_launches, "clocks": clocks}
+    line.update(extras)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -181,6 +181,28 @@ int pf_diagnostics(pf_handle *h, double out[8]);
 int pf_solve_helmholtz(pf_handle *h, int bcset, int mode, double lambda,
                        const double *rhs, double *out);
 
+/* Kernel classes of the per-class launch counters and timers (pf_profile_read). */
+#define PF_KC_GEMM      0   /* fast-diagonalisation transforms (4 per solve batch)          */
+#define PF_KC_FWD       1   /* direct stiffness summation + forward z FFT + combination     */
+#define PF_KC_INV       2   /* inverse z FFT (+ d/dz, Dirichlet values)                     */
+#define PF_KC_POTENTIAL 3   /* eq. 54a/74a right-hand side                                  */
+#define PF_KC_CHEM      4   /* eq. 56/75 right-hand side                                    */
+#define PF_KC_MOMENTUM  5   /* eq. 49, 58a/77a, 59a/78a right-hand sides                    */
+#define PF_KC_UGRADP    6   /* new-pressure term of eq. 59a/78a                             */
+#define PF_KC_EFIELD    7   /* eq. 55/78 projection                                         */
+#define PF_KC_OTHER     8   /* phi right-hand side, wall-face transform, conversions        */
+#define PF_KC_COUNT     9
+
+/* Enable (1) or disable (0) per-class CUDA-event timing of the kernels this handle
+ * launches (events bracket every launch on the handle's stream, so enabling it adds a
+ * little host overhead).  Enabling resets the timers.  Launch counters always run. */
+int pf_profile(pf_handle *h, int enable);
+
+/* Read the counters (synchronous): ms[PF_KC_COUNT] = summed device time per class since
+ * timing was enabled (0 when disabled), launches[PF_KC_COUNT] = kernels launched per
+ * class since creation.  Either pointer may be NULL. */
+int pf_profile_read(pf_handle *h, double *ms, long long *launches);
+
 /* Geometry queries: nodes_x[n_x], nodes_y[n_y] (either may be NULL), sizes in dims[4]
  * = {n_x, n_y, Nz, number of real values per field}. */
 int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]);

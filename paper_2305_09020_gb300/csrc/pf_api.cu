@@ -79,9 +79,62 @@ T *dupload(const std::vector<double> &v, cudaStream_t st) {
     return d;
 }
 
+// Per-class launch counters and optional CUDA-event timers of the kernels a handle launches.
+struct Prof {
+    bool on = false;
+    long long launches[PF_KC_COUNT] = {};
+    double ms[PF_KC_COUNT] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    cudaEvent_t ev_begin = nullptr;
+    int kc_open = -1;
+
+    cudaEvent_t take() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            PF_CU(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(int kc, cudaStream_t st) {
+        launches[kc] += 1;
+        if (!on) return;
+        ev_begin = take();
+        kc_open = kc;
+        PF_CU(cudaEventRecord(ev_begin, st));
+    }
+    void end(cudaStream_t st) {
+        if (!on || kc_open < 0) return;
+        cudaEvent_t e = take();
+        PF_CU(cudaEventRecord(e, st));
+        pending.push_back({kc_open, {ev_begin, e}});
+        kc_open = -1;
+        if (pending.size() > 4096) resolve();
+    }
+    void resolve() {
+        for (auto &p : pending) {
+            PF_CU(cudaEventSynchronize(p.second.second));
+            float t = 0.f;
+            PF_CU(cudaEventElapsedTime(&t, p.second.first, p.second.second));
+            ms[p.first] += t;
+            pool.push_back(p.second.first);
+            pool.push_back(p.second.second);
+        }
+        pending.clear();
+    }
+    ~Prof() {
+        for (auto &p : pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 template <typename T>
 struct Engine {
     const HostSetup &hs;
+    Prof *prof = nullptr;
     cudaStream_t st;
     int ex, ey, K, p, nx, ny, n2, nz;
     long long N, NL;
@@ -114,7 +167,7 @@ struct Engine {
         return q;
     }
 
-    Engine(const HostSetup &s, cudaStream_t stream) : hs(s), st(stream) {
+    Engine(const HostSetup &s, cudaStream_t stream, Prof *pr) : hs(s), prof(pr), st(stream) {
         ex = s.ex; ey = s.ey; K = s.K; p = s.p; nx = s.nx; ny = s.ny; nz = s.nz;
         n2 = nx * ny;
         N = (long long)n2 * nz;
@@ -235,8 +288,10 @@ struct Engine {
         pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod};
         constexpr int BM = 64, BN = 64, BK = sizeof(T) == 8 ? 8 : 16;
         dim3 grid((Ncol + BN - 1) / BN, (unsigned)((Mrows + BM - 1) / BM));
+        prof->begin(PF_KC_GEMM, st);
         pf::k_gemm<T, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g);
         check_launch();
+        prof->end(st);
     }
 
     // fast-diagonalisation solve of nplanes mode planes: out = S_y [ (S_y^T rhs S_x) / (L_y + L_x + c_p) ] S_x^T
@@ -255,8 +310,10 @@ struct Engine {
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        prof->begin(PF_KC_FWD, st);
         pf::k_fwd<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
         check_launch();
+        prof->end(st);
     }
 
     void inv(const T *Y, T *out, T *dzout, int drow0, double v0, int drow1, double v1) {
@@ -265,8 +322,10 @@ struct Engine {
         a.out = out; a.dzout = d3 ? dzout : nullptr; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        prof->begin(PF_KC_INV, st);
         pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
         check_launch();
+        prof->end(st);
     }
 
     void inv_phi(double alpha, T *phi_out, T *dzphi_out) {
@@ -277,8 +336,10 @@ struct Engine {
         a.out3 = Lf; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz); a.tw = tw;
         a.tp = std::max(4, fwd_tp() / 2);
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>);
+        prof->begin(PF_KC_INV, st);
         pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
         check_launch();
+        prof->end(st);
     }
 
     // ---- the potential sub-step (also used by the initial fixed point) ----------------------
@@ -286,9 +347,11 @@ struct Engine {
                    T *Vout, T *Ezout) {
         auto G = geo();
         auto q = phys(J);
+        prof->begin(PF_KC_POTENTIAL, st);
         pf::k_potential<T><<<elem_grid(), elem_threads(), elem_smem(3), st>>>(G, q, phin, phio, Vn, Vo, Ezn,
                                                                             Ezo, LA, d3 ? LB : nullptr);
         check_launch();
+        prof->end(st);
         fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_V, shV, nz);
         inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
@@ -296,8 +359,10 @@ struct Engine {
 
     void efield(const T *Vf) {
         const long long tot = N;
+        prof->begin(PF_KC_EFIELD, st);
         pf::k_efield<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(geo(), Vf, Ex, Ey);
         check_launch();
+        prof->end(st);
     }
 
     // ---- one time step -----------------------------------------------------------------------
@@ -310,10 +375,12 @@ struct Engine {
         potential(J, phi[n], phi[o], V[n], V[o], Ez[n], Ez[o], V[o], Ez[o]);
         efield(V[o]);
         // psi^{n+1}
+        prof->begin(PF_KC_CHEM, st);
         pf::k_chem<T><<<elem_grid(), elem_threads(), elem_smem(4), st>>>(
             G, q, phi[n], phi[o], dzphi[n], dzphi[o], u[0][n], u[0][o], u[1][n], u[1][o], u[2][n], u[2][o], Ex,
             Ey, Ez[o], LA, Q2, q.wetting ? faceU : nullptr);
         check_launch();
+        prof->end(st);
         fwd(LA, 1, Q2, 0, 1, 1.0, nullptr, RHS, Q2H);
         fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz);
         // phi^{n+1}
@@ -321,12 +388,16 @@ struct Engine {
         if (q.wetting) {
             const int tp = fwd_tp();
             const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + tp * (nz + 1)) * sizeof(cplx<T>);
+            prof->begin(PF_KC_OTHER, st);
             pf::k_face_fft<T><<<(nx + tp - 1) / tp, 256, smem, st>>>(G, faceU, FACEH, tw, tp);
             check_launch();
+            prof->end(st);
             faceh = FACEH;
         }
+        prof->begin(PF_KC_OTHER, st);
         pf::k_rhs_phi<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G, PSIH, faceh, RHS);
         check_launch();
+        prof->end(st);
         fdm(RHS, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
         inv_phi(al, phi[o], dzphi[o]);
         // P^{n+1}
@@ -340,15 +411,19 @@ struct Engine {
         pf::MomOut<T> mo;
         mo.AP = LA; mo.BP = d3 ? LB : nullptr;
         for (int c = 0; c < 3; ++c) { mo.AU[c] = LAU[c]; mo.BU[c] = LBU[c]; }
+        prof->begin(PF_KC_MOMENTUM, st);
         pf::k_momentum<T><<<elem_grid(), elem_threads(), elem_smem(12), st>>>(G, q, mi, mo);
         check_launch();
+        prof->end(st);
         fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_P, shP, nz);
         inv(OUT, P[o], dzP[o], -1, 0.0, -1, 0.0);
         // u^{n+1}
+        prof->begin(PF_KC_UGRADP, st);
         pf::k_ugradp<T><<<elem_grid(), elem_threads(), elem_smem(1), st>>>(G, q, P[o], LAU[0], LAU[1],
                                                                          d3 ? LBU[2] : nullptr);
         check_launch();
+        prof->end(st);
         const int dc = d3 ? 3 : 2;
         for (int c = 0; c < dc; ++c) fwd(LAU[c], 1, d3 ? LBU[c] : nullptr, 1, 0, 1.0, nullptr, RHS + c * N, nullptr);
         fdm(RHS, OUT, PF_BCSET_U, shU[J - 1], dc * nz);
@@ -379,6 +454,7 @@ struct Engine {
 
 struct pf_handle {
     HostSetup hs;
+    Prof prof;
     cudaStream_t st = nullptr;
     std::unique_ptr<Engine<double>> e64;
     std::unique_ptr<Engine<float>> e32;
@@ -492,19 +568,27 @@ void copy_level(Engine<T> &E, int from, int to) {
     for (int c = 0; c < 3; ++c) { cp(E.u[c]); cp(E.dzu[c]); }
 }
 
+// Host <-> device field copies: the caller's double buffer is copied as is (DMA directly
+// from/to it when it is pinned) into device scratch and converted there.
 template <typename T>
 void upload_field(Engine<T> &E, T *dst, const double *host) {
-    std::vector<T> h(host, host + E.N);
-    PF_CU(cudaMemcpyAsync(dst, h.data(), E.N * sizeof(T), cudaMemcpyHostToDevice, E.st));
-    PF_CU(cudaStreamSynchronize(E.st));
+    double *scratch = reinterpret_cast<double *>(E.W2);   // 3N values of T >= N doubles
+    PF_CU(cudaMemcpyAsync(scratch, host, E.N * sizeof(double), cudaMemcpyHostToDevice, E.st));
+    E.prof->begin(PF_KC_OTHER, E.st);
+    pf::k_convert<double, T><<<1024, 256, 0, E.st>>>(scratch, dst, E.N);
+    PF_CU(cudaGetLastError());
+    E.prof->end(E.st);
 }
 
 template <typename T>
 void download_field(Engine<T> &E, const T *src, double *host) {
-    std::vector<T> h(E.N);
-    PF_CU(cudaMemcpyAsync(h.data(), src, E.N * sizeof(T), cudaMemcpyDeviceToHost, E.st));
+    double *scratch = reinterpret_cast<double *>(E.W2);
+    E.prof->begin(PF_KC_OTHER, E.st);
+    pf::k_convert<T, double><<<1024, 256, 0, E.st>>>(src, scratch, E.N);
+    PF_CU(cudaGetLastError());
+    E.prof->end(E.st);
+    PF_CU(cudaMemcpyAsync(host, scratch, E.N * sizeof(double), cudaMemcpyDeviceToHost, E.st));
     PF_CU(cudaStreamSynchronize(E.st));
-    for (long long i = 0; i < E.N; ++i) host[i] = (double)h[i];
 }
 
 // z-derivative of a physical field through the engine's own transforms (forward then
@@ -594,7 +678,7 @@ extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vb
     h->st = (cudaStream_t)cuda_stream;
     try {
         // the initial potential always runs in FP64
-        std::unique_ptr<Engine<double>> e64(new Engine<double>(s, h->st));
+        std::unique_ptr<Engine<double>> e64(new Engine<double>(s, h->st, &h->prof));
         engine_init_state(h.get(), *e64, phi0, u0);
         int rc = initial_potential(h.get(), *e64, e64->phi[0]);
         if (rc != PF_OK) { g_create_error = h->err; return rc; }
@@ -604,7 +688,7 @@ extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vb
         if (s.precision == PF_FP64) {
             h->e64 = std::move(e64);
         } else {
-            std::unique_ptr<Engine<float>> e32(new Engine<float>(s, h->st));
+            std::unique_ptr<Engine<float>> e32(new Engine<float>(s, h->st, &h->prof));
             auto cv = [&](const double *src, float *dst) {
                 if (!src || !dst) return;
                 pf::k_convert<double, float><<<1024, 256, 0, h->st>>>(src, dst, e64->N);
@@ -823,6 +907,35 @@ extern "C" int pf_solve_helmholtz(pf_handle *h, int bcset, int mode, double lamb
     } catch (const CudaError &e) {
         return cuda_fail(h, e);
     }
+}
+
+extern "C" int pf_profile(pf_handle *h, int enable) {
+    if (!h) return PF_EINVAL;
+    try {
+        PF_CU(cudaStreamSynchronize(h->st));
+        h->prof.resolve();
+        h->prof.on = enable != 0;
+        if (h->prof.on)
+            for (int k = 0; k < PF_KC_COUNT; ++k) h->prof.ms[k] = 0.0;
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_profile_read(pf_handle *h, double *ms, long long *launches) {
+    if (!h) return PF_EINVAL;
+    try {
+        PF_CU(cudaStreamSynchronize(h->st));
+        h->prof.resolve();
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+    for (int k = 0; k < PF_KC_COUNT; ++k) {
+        if (ms) ms[k] = h->prof.on ? h->prof.ms[k] : 0.0;
+        if (launches) launches[k] = h->prof.launches[k];
+    }
+    return PF_OK;
 }
 
 extern "C" int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]) {

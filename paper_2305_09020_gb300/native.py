@@ -23,6 +23,7 @@ PF_FP64, PF_MIXED = 0, 1
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64
+KERNEL_CLASSES = ["gemm", "fwd", "inv", "potential", "chem", "momentum", "ugradp", "efield", "other"]
 _BLOCKS = [(PF_FIELD_V, ["V"]), (PF_FIELD_E, ["Ex", "Ey", "Ez"]), (PF_FIELD_PHI, ["phi"]),
            (PF_FIELD_PSI, ["psi"]), (PF_FIELD_P, ["P"]), (PF_FIELD_U, ["ux", "uy", "uz"])]
 
@@ -83,6 +84,8 @@ def load(build_if_missing: bool = True):
     L.pf_diagnostics.argtypes = [c_void_p, dp]
     L.pf_solve_helmholtz.argtypes = [c_void_p, c_int, c_int, c_double, dp, dp]
     L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
+    L.pf_profile.argtypes = [c_void_p, c_int]
+    L.pf_profile_read.argtypes = [c_void_p, dp, POINTER(ctypes.c_longlong)]
     L.pf_destroy.argtypes = [c_void_p]
     L.pf_destroy.restype = None
     L.pf_last_error.argtypes = [c_void_p]
@@ -195,6 +198,13 @@ class Solver:
         shp = (self.nz, self.ny, self.nx)
         return {nm: out[i * self.n:(i + 1) * self.n].reshape(shp) for i, nm in enumerate(names)}
 
+    def get_into(self, mask: int, out: np.ndarray):
+        """Copy fields into a caller-provided (e.g. pinned) float64 buffer, no allocation."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array")
+        _check(load().pf_get_fields(self._h, int(mask), _dp(out), out.size), self._h)
+        return out
+
     def set(self, mask: int, data: np.ndarray, reset_history: bool = False):
         data = _f64(data).ravel()
         _check(load().pf_set_fields(self._h, int(mask), _dp(data), data.size, int(reset_history)), self._h)
@@ -209,6 +219,15 @@ class Solver:
         out = np.zeros_like(rhs)
         _check(load().pf_solve_helmholtz(self._h, int(bcset), int(mode), float(lam), _dp(rhs), _dp(out)), self._h)
         return out
+
+    def profile(self, enable: bool):
+        _check(load().pf_profile(self._h, int(bool(enable))), self._h)
+
+    def profile_read(self):
+        ms = np.zeros(len(KERNEL_CLASSES))
+        ln = (ctypes.c_longlong * len(KERNEL_CLASSES))()
+        _check(load().pf_profile_read(self._h, _dp(ms), ln), self._h)
+        return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def geometry(self):
         x, y = np.zeros(self.nx), np.zeros(self.ny)
