@@ -207,6 +207,34 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
  * = {n_x, n_y, Nz, number of real values per field}. */
 int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]);
 
+/* ---- allocation-free solve ---------------------------------------------------------- */
+
+/* Capacity, in doubles, of each of the two scratch buffers of pf_fdm_solve_static. */
+#define PF_STATIC_MAX_VALUES (1 << 20)
+
+/* A fast-diagonalisation solve that allocates nothing, for callers that cannot call
+ * cudaMalloc where they need it (inside a region where allocation is forbidden or would
+ * synchronise the device, a memory-planned real-time loop, a host library that brings its
+ * own allocator).  The paper has no counterpart: it is a packaging of the solve above.
+ *
+ * For each of nplanes planes p ([p][y][x], x fastest, device memory) it computes
+ *   out[p] = Sy [ (Sy^T rhs[p] Sx) / (lam_y[i] + lam_x[j] + shift[p]) ] Sx^T
+ * in FP64, i.e. the solution of (K + shift[p] M) x = rhs[p] when rhs[p] is the weak-form
+ * (mass-weighted) right-hand side and Sx, Sy, lam_x, lam_y are the factors returned by
+ * pf_fdm_1d (SxT, SyT their transposes, row-major; a zero denominator gives 0).
+ * Every pointer is a caller-owned device pointer; the call is asynchronous on cuda_stream.
+ *
+ * Its two intermediate buffers live in one file-scope device array of
+ * 2 * PF_STATIC_MAX_VALUES doubles (16 MiB) that every GPU loading this library holds
+ * until exit.  nx*ny*nplanes > PF_STATIC_MAX_VALUES returns PF_EINVAL (message in
+ * pf_last_error(NULL)).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call shares the array, so calls that overlap on the GPU (other streams,
+ * other threads) race; each call fully overwrites the buffers before reading them. */
+int pf_fdm_solve_static(int nx, int ny, int nplanes, const double *Sx, const double *SxT,
+                        const double *lam_x, const double *Sy, const double *SyT, const double *lam_y,
+                        const double *shift, const double *rhs, double *out, void *cuda_stream);
+
 /* Release all device memory of the handle (NULL is a no-op). */
 void pf_destroy(pf_handle *h);
 

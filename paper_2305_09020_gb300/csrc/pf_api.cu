@@ -452,6 +452,9 @@ struct Engine {
 
 }  // namespace
 
+// message of the last failed call that has no handle (read with pf_last_error(NULL))
+void pf_internal_set_error(const std::string &msg) { g_create_error = msg; }
+
 struct pf_handle {
     HostSetup hs;
     Prof prof;

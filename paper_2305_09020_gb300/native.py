@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     L.pf_solve_helmholtz.argtypes = [c_void_p, c_int, c_int, c_double, dp, dp]
     L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
     L.pf_profile.argtypes = [c_void_p, c_int]
+    L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_profile_read.argtypes = [c_void_p, dp, POINTER(ctypes.c_longlong)]
     L.pf_destroy.argtypes = [c_void_p]
     L.pf_destroy.restype = None
@@ -144,6 +145,19 @@ def fdm_1d(Kmat, Mdiag, dirichlet=None):
     S, lam = np.zeros((n, n)), np.zeros(n)
     _check(L.pf_fdm_1d(n, _dp(Kmat), _dp(Mdiag), mask.ctypes.data_as(POINTER(c_ubyte)), _dp(S), _dp(lam)))
     return S, lam
+
+
+PF_STATIC_MAX_VALUES = 1 << 20
+
+
+def fdm_solve_static(nx: int, ny: int, nplanes: int, Sx, SxT, lam_x, Sy, SyT, lam_y, shift, rhs, out,
+                     stream: Optional[int] = None):
+    """Allocation-free FP64 fast-diagonalisation solve; every array argument is a device
+    pointer (int), e.g. ``tensor.data_ptr()`` of a float64 CUDA tensor."""
+    L = load()
+    ptrs = [c_void_p(int(p)) for p in (Sx, SxT, lam_x, Sy, SyT, lam_y, shift, rhs, out)]
+    rc = L.pf_fdm_solve_static(int(nx), int(ny), int(nplanes), *ptrs, c_void_p(stream or 0))
+    _check(rc, None)
 
 
 # ---- the time stepper -------------------------------------------------------------------------
