@@ -137,7 +137,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -159,7 +159,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    prec = native.PF_MIXED if args.precision == "mixed" else native.PF_FP64
+    prec = {"mixed": native.PF_MIXED, "mixed_simt": native.PF_MIXED_SIMT, "fp64": native.PF_FP64}[args.precision]
     wl = workloads.droplet3d()
     m = wl.mesh
     nx, ny, nz = m.ex * m.order, m.ey * m.order + 1, m.nz
@@ -217,13 +217,21 @@ def main():
             nlaunch = cls["gemm"][1] - launches1["gemm"][1]
             achieved = flops / nlaunch / (per_launch_ms * 1e-3) / 1e12
             if prec == native.PF_MIXED:
+                # 3xTF32 on tcgen05: TF32 dense peak = measured bf16 peak x nominal TF32/BF16 (1.1/2.25)
+                peak = pk["bf16_tflops"] * (1.1 / 2.25)
+                roof = {"bound": "tensor", "kernel": "k_gemm_tc (3xTF32 fast-diagonalisation transforms)",
+                        "peak_source": f"{src} bf16 {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (TF32 dense); achieved "
+                                       "counts the FP32 GEMM flops, 3 TF32 MMAs are issued per useful product"}
+            elif prec == native.PF_MIXED_SIMT:
                 peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                roof = {"bound": "alu", "kernel": "k_gemm (FP32 SIMT fast-diagonalisation transforms)",
+                        "peak_source": f"derived: {SM_COUNT} SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
             else:
                 peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "kernel": "k_gemm (fast-diagonalisation transforms)", "achieved": achieved,
-                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"derived: {SM_COUNT} SMs x {'128 FP32 FMA' if prec == native.PF_MIXED else '2 FP64 FMA'}"
-                                   f"/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+                roof = {"bound": "alu", "kernel": "k_gemm (FP64 SIMT fast-diagonalisation transforms)",
+                        "peak_source": f"derived: {SM_COUNT} SMs x 2 FP64 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+            roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None})
         else:
             roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None, "peak_source": src}
@@ -258,7 +266,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == native.PF_MIXED else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == native.PF_FP64 else "f32",
             "data": "synthetic",
             "config": {"workload": "droplet3d: 16x8 elements order 8 x Nz=64 planes, sphere r=0.25 on the "
                                    "electrode, eps/rho/mu ratios 10/2/5, V=2, dt=5e-5",

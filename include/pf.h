@@ -52,8 +52,10 @@ extern "C" {
 #define PF_BC_NEUMANN   1
 
 #define PF_FP64  0   /* every kernel in double precision                                  */
-#define PF_MIXED 1   /* node-wise kernels, FFT and eigenbasis GEMMs in single precision;  */
-                     /* set-up, the initial-potential fixed point and reductions in FP64  */
+#define PF_MIXED 1   /* node-wise kernels and FFT in FP32, eigenbasis GEMMs in 3xTF32 on   */
+                     /* the tensor cores (FP32 accumulation); set-up, the initial-potential */
+                     /* fixed point and reductions in FP64                                  */
+#define PF_MIXED_SIMT 2  /* as PF_MIXED but the eigenbasis GEMMs on the FP32 SIMT pipe     */
 
 /* boundary-condition sets of the Helmholtz solves (y-direction; x is periodic) */
 #define PF_BCSET_V   0   /* the potential: per-side Dirichlet/Neumann from pf_vbc           */
@@ -100,7 +102,7 @@ typedef struct {
 typedef struct {
     double dt;          /* time step                                                       */
     int bdf;            /* 1 or 2 (BDF order J of Sec. 3.1; J = 1 is used for step 1)      */
-    int precision;      /* PF_FP64 or PF_MIXED                                             */
+    int precision;      /* PF_FP64, PF_MIXED or PF_MIXED_SIMT                              */
     double S;           /* stabiliser; 0 -> eta^2 sqrt(4 gamma0 / (lambda gamma1 dt))      */
     double nu_m;        /* 0 -> max(mu1,mu2)/min(rho1,rho2)                                */
     double rho0;        /* 0 -> min(rho1,rho2)                                             */

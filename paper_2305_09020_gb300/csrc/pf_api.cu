@@ -20,6 +20,7 @@
 
 #include "../../include/pf.h"
 #include "pf_kernels.cuh"
+#include "pf_tc.cuh"
 
 using pf::cplx;
 
@@ -152,7 +153,52 @@ struct Engine {
     T *LA, *LB, *LAU[3], *LBU[3], *faceU;
     T *RHS, *OUT, *PSIH, *Q2H, *FACEH, *W1, *W2;
     double *red;
+    int *dev_err;   // device error word (bounded waits)
     int cur = 0;
+    // 3xTF32 tensor-core operands: for each B matrix of the transforms, B^T split into
+    // TF32 head/tail, zero padded to Npad x Kpad
+    struct TcB {
+        const T *key;
+        float *hi, *lo;
+        int N, Npad, Kpad, ntile, tile_n, cols;
+        size_t smem;
+    };
+    std::vector<TcB> tcb;
+    bool use_tc = false;
+    // steady-state (BDF2) step captured once per history-slot parity; replayed by pf_step
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches[2][PF_KC_COUNT] = {};
+
+    // one BDF2 step through the captured graph of the current slot parity (captured on first use)
+    void step_graph() {
+        const int c = cur;
+        if (!graph[c]) {
+            long long before[PF_KC_COUNT];
+            for (int k = 0; k < PF_KC_COUNT; ++k) before[k] = prof->launches[k];
+            cudaGraph_t g = nullptr;
+            PF_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            try {
+                step(2);
+            } catch (...) {
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                cur = c;
+                throw;
+            }
+            PF_CU(cudaStreamEndCapture(st, &g));
+            cudaError_t e = cudaGraphInstantiate(&graph[c], g, 0);
+            cudaGraphDestroy(g);
+            PF_CU(e);
+            for (int k = 0; k < PF_KC_COUNT; ++k) {
+                graph_launches[c][k] = prof->launches[k] - before[k];
+                prof->launches[k] = before[k];
+            }
+            cur = c;   // the capture did not run anything
+        }
+        PF_CU(cudaGraphLaunch(graph[c], st));
+        for (int k = 0; k < PF_KC_COUNT; ++k) prof->launches[k] += graph_launches[c][k];
+        cur = 1 - c;
+    }
 
     template <typename U>
     U *mk(size_t n) {
@@ -247,15 +293,80 @@ struct Engine {
         RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
         red = mk<double>(1024);
+        dev_err = mk<int>(1);
+        use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED;
+        if (use_tc) {
+            // B = Sx (Bt = Sx^T), B = Sx^T (Bt = Sx), B = Sy (Bt = Sy^T), B = Sy^T (Bt = Sy)
+            auto tr = [](const std::vector<double> &m, int n) {
+                std::vector<double> t((size_t)n * n);
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) t[(size_t)i * n + j] = m[(size_t)j * n + i];
+                return t;
+            };
+            add_tc(Sx, tr(s.Sx, nx), nx);
+            add_tc(SxT, s.Sx, nx);
+            for (int b = 0; b < 4; ++b) {
+                add_tc(Sy[b], tr(s.Sy[b], ny), ny);
+                add_tc(SyT[b], s.Sy[b], ny);
+            }
+            PF_CU(cudaFuncSetAttribute(pf::k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(16)));
+        }
         PF_CU(cudaStreamSynchronize(st));
     }
+
+    // host TF32 rounding to nearest, ties away from zero (the rounding of cvt.rna.tf32.f32)
+    static float tf32_rna_host(float x) {
+        uint32_t u;
+        std::memcpy(&u, &x, 4);
+        if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+        float r;
+        std::memcpy(&r, &u, 4);
+        return r;
+    }
+
+    // Bt (n x n row-major, FP64) -> TF32 head/tail on the device, rows padded to a multiple of 64
+    // (the column tiles) and K padded to a multiple of 32 (the chunks)
+    void add_tc(const T *key, const std::vector<double> &Bt, int n) {
+        TcB t;
+        t.key = key;
+        t.N = n;
+        t.Npad = (n + 63) / 64 * 64;
+        t.Kpad = (n + 31) / 32 * 32;
+        t.ntile = 0; t.tile_n = 0; t.cols = 0; t.smem = 0;
+        std::vector<float> hi((size_t)t.Npad * t.Kpad, 0.f), lo((size_t)t.Npad * t.Kpad, 0.f);
+        for (int r = 0; r < n; ++r)
+            for (int k = 0; k < n; ++k) {
+                const double v = Bt[(size_t)r * n + k];
+                const float h = tf32_rna_host((float)v);
+                hi[(size_t)r * t.Kpad + k] = h;
+                lo[(size_t)r * t.Kpad + k] = tf32_rna_host((float)(v - (double)h));
+            }
+        t.hi = mk<float>(hi.size());
+        t.lo = mk<float>(lo.size());
+        PF_CU(cudaMemcpyAsync(t.hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, st));
+        PF_CU(cudaMemcpyAsync(t.lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
+        PF_CU(cudaStreamSynchronize(st));
+        tcb.push_back(t);
+    }
+
+    // dynamic shared memory of k_gemm_tc<TN>: two stages of A and Bt (hi, lo), barrier, slack;
+    // at least a third of the SM so that at most two CTAs (2 x 16 TN <= 512 TMEM columns for
+    // TN <= 16) share one
+    static size_t tc_smem(int TN) {
+        const size_t need = (size_t)2 * (2 * 128 * 32 * 4 + 2 * TN * 32 * 4) + 16 + 1024;
+        return std::max(need, (size_t)233472 / 3 + 1024);
+    }
+
     ~Engine() {
+        for (int c = 0; c < 2; ++c)
+            if (graph[c]) cudaGraphExecDestroy(graph[c]);
         for (void *q : allocs) cudaFree(q);
     }
 
     pf::Geo<T> geo() const {
         pf::Geo<T> g;
         g.ex = ex; g.ey = ey; g.K = K; g.p = p; g.nx = nx; g.ny = ny; g.n2 = n2; g.nz = nz;
+        g.epb = epb();
         g.hx = hx; g.hy = hy; g.D = D; g.Dw = Dw; g.w = w; g.Mx = Mx; g.My = My;
         return g;
     }
@@ -272,11 +383,18 @@ struct Engine {
     }
 
     // ---- launch helpers -----------------------------------------------------------------
-    int elem_threads() const { return ((p * p + 31) / 32) * 32; }
-    size_t elem_smem(int nfields) const { return (size_t)(2 * p * p + 32 + nfields * p * p) * sizeof(T); }
-    dim3 elem_grid() const { return dim3(ex * ey, nz); }
+    // element kernels: as many whole elements as fit in 256 threads per block
+    int epb() const { return std::max(1, 256 / (p * p)); }
+    int elem_threads() const { return ((epb() * p * p + 31) / 32) * 32; }
+    size_t elem_smem(int nfields) const {
+        return (size_t)(2 * p * p + 32 + (size_t)epb() * nfields * p * p) * sizeof(T);
+    }
+    dim3 elem_grid() const { return dim3((ex * ey + epb() - 1) / epb(), nz); }
+    // pencils per transform block: enough blocks for 4 per SM, shared memory <= 24 KiB
     int fwd_tp() const {
         int tp = (int)(24576 / (sizeof(cplx<T>) * (nz + 1)));
+        const int by_grid = n2 / (4 * 152);
+        if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;
         if (tp < 4) tp = 4;
         return tp;
@@ -285,11 +403,40 @@ struct Engine {
 
     void gemm(const T *A, const T *B, T *C, long long Mrows, int Ncol, int R, int store, const T *lamN,
               const T *lamR, const T *cpl, int cpl_mod) {
+        if (use_tc) {
+            for (auto &t : tcb) {
+                if (t.key != B) continue;
+                pf::TcArgs a;
+                a.A = reinterpret_cast<const float *>(A);
+                a.Bhi = t.hi; a.Blo = t.lo;
+                a.C = reinterpret_cast<float *>(C);
+                a.Mrows = Mrows; a.Kd = Ncol; a.N = Ncol; a.Npad = t.Npad; a.Kpad = t.Kpad;
+                a.ntile = 0; a.tile_n = 0; a.tmem_cols = 0;
+                a.R = R; a.store = store;
+                a.lamN = reinterpret_cast<const float *>(lamN);
+                a.lamR = reinterpret_cast<const float *>(lamR);
+                a.cpl = reinterpret_cast<const float *>(cpl);
+                a.cpl_mod = cpl_mod; a.err = dev_err;
+                const unsigned mt = (unsigned)((Mrows + 127) / 128);
+                prof->begin(PF_KC_GEMM, st);
+                pf::k_gemm_tc<16><<<dim3(mt, (Ncol + 15) / 16), 128, tc_smem(16), st>>>(a);
+                check_launch();
+                prof->end(st);
+                return;
+            }
+        }
         pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod};
-        constexpr int BM = 64, BN = 64, BK = sizeof(T) == 8 ? 8 : 16;
-        dim3 grid((Ncol + BN - 1) / BN, (unsigned)((Mrows + BM - 1) / BM));
+        constexpr int BK = sizeof(T) == 8 ? 8 : 16;
+        const long long tiles64 = ((Ncol + 63) / 64) * ((Mrows + 63) / 64);
         prof->begin(PF_KC_GEMM, st);
-        pf::k_gemm<T, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g);
+        if (tiles64 >= 4 * 152 && Ncol % 64 > 32) {
+            dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 63) / 64));
+            pf::k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(g);
+        } else {
+            // small or ragged problems: 32x32 tiles give 4x the blocks and less padding
+            dim3 grid((Ncol + 31) / 32, (unsigned)((Mrows + 31) / 32));
+            pf::k_gemm<T, 32, 32, BK, 2, 2><<<grid, 256, 0, st>>>(g);
+        }
         check_launch();
         prof->end(st);
     }
@@ -309,7 +456,7 @@ struct Engine {
         a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int);
         prof->begin(PF_KC_FWD, st);
         pf::k_fwd<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
         check_launch();
@@ -620,7 +767,9 @@ template <typename T>
 int do_steps(pf_handle *h, Engine<T> &E, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         const int J = (h->nstep == 0 || h->hs.bdf == 1) ? 1 : 2;
-        E.step(J);
+        // graphs need a capturable stream (not the legacy default stream) and no event timers
+        if (J == 2 && E.st != nullptr && !h->prof.on) E.step_graph();
+        else E.step(J);
         h->last_J = J;
         h->nstep += 1;
         h->t += h->hs.dt;
@@ -654,7 +803,8 @@ extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vb
           f.eta > 0 && f.gamma1 > 0))
         return fail(nullptr, PF_EINVAL, "fluid parameters must be positive");
     if (!(scheme->dt > 0) || (scheme->bdf != 1 && scheme->bdf != 2)) return fail(nullptr, PF_EINVAL, "bad dt or bdf");
-    if (scheme->precision != PF_FP64 && scheme->precision != PF_MIXED) return fail(nullptr, PF_EINVAL, "bad precision");
+    if (scheme->precision != PF_FP64 && scheme->precision != PF_MIXED && scheme->precision != PF_MIXED_SIMT)
+        return fail(nullptr, PF_EINVAL, "bad precision");
 
     std::unique_ptr<pf_handle> h(new pf_handle());
     HostSetup &s = h->hs;

@@ -43,6 +43,7 @@ __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
 template <typename T>
 struct Geo {
     int ex, ey, K, p, nx, ny, n2, nz;
+    int epb;            // elements per block of the element kernels
     const T *hx, *hy;   // element sizes
     const T *D;         // D[a*p+m] = l_m'(xi_a)
     const T *Dw;        // Dw[a*p+c] = w_a D[a*p+c]
@@ -84,25 +85,31 @@ template <typename T> __device__ __forceinline__ T hatv(int J, T a, T b) { retur
 
 // ---- element helpers ----------------------------------------------------------------------
 struct ElemIdx {
-    int ex, ey, a, b, t, z;
+    int ex, ey, a, b, t, z, le;
+    bool act;       // this thread owns a node of an existing element
     long long g;    // global nodal index (with plane offset)
     long long l;    // element-local slot (with plane offset)
 };
 
+// blockIdx.x: group of G.epb elements of plane blockIdx.y; thread = (local element, node)
 template <typename T>
 __device__ __forceinline__ ElemIdx elem_index(const Geo<T> &G) {
     ElemIdx e;
-    const int el = blockIdx.x;
+    const int pp = G.p * G.p;
+    e.le = threadIdx.x / pp;
+    e.t = threadIdx.x - e.le * pp;
+    const int el = blockIdx.x * G.epb + e.le;
+    e.act = e.le < G.epb && el < G.ex * G.ey;
+    const int elc = e.act ? el : 0;
     e.z = blockIdx.y;
-    e.ex = el % G.ex;
-    e.ey = el / G.ex;
-    e.t = threadIdx.x;
+    e.ex = elc % G.ex;
+    e.ey = elc / G.ex;
     e.a = e.t % G.p;
     e.b = e.t / G.p;
     int xi = e.ex * G.K + e.a;
     if (xi >= G.nx) xi -= G.nx;
     e.g = (long long)e.z * G.n2 + (long long)(e.ey * G.K + e.b) * G.nx + xi;
-    e.l = ((long long)e.z * G.ex * G.ey + el) * (G.p * G.p) + e.t;
+    e.l = ((long long)e.z * G.ex * G.ey + elc) * pp + e.t;
     return e;
 }
 
@@ -144,14 +151,15 @@ __device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, i
     return s * hx2 * sw[a];
 }
 
+// shared memory: D, Dw, w tables, then nfields element arrays per local element
 #define PF_ELEM_SMEM(T, G, nfields)                                                   \
     extern __shared__ unsigned char pf_smem_raw[];                                    \
     T *sD = reinterpret_cast<T *>(pf_smem_raw);                                       \
     T *sDw = sD + (G).p * (G).p;                                                      \
     T *sw = sDw + (G).p * (G).p;                                                      \
-    T *sF = sw + 32;                                                                  \
     const int pp_ = (G).p * (G).p;                                                    \
-    (void)pp_;
+    const int le_ = min((int)(threadIdx.x / pp_), (G).epb - 1);                      \
+    T *sF = sw + 32 + le_ * (nfields) * pp_;
 
 // ---- eq. 54a / 74a: RHS of the potential --------------------------------------------------
 // A = -int R_2D . grad_2D w  (element-local contributions),  B = int R_z w  (iB multiplier)
@@ -164,7 +172,7 @@ __global__ void k_potential(Geo<T> G, Phys<T> q, const T *__restrict__ phin, con
     T *sV = sF, *sRx = sF + pp_, *sRy = sF + 2 * pp_;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
-    const bool act = e.t < pp_;
+    const bool act = e.act;
     const T hx = G.hx[e.ex], hy = G.hy[e.ey];
     T phis = 0, Vs = 0;
     if (act) {
@@ -256,7 +264,7 @@ __global__ void k_chem(Geo<T> G, Phys<T> q, const T *__restrict__ phin, const T 
     T *sP = sF, *sQ = sF + pp_, *sQx = sF + 2 * pp_, *sQy = sF + 3 * pp_;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
-    const bool act = e.t < pp_;
+    const bool act = e.act;
     const T hx = G.hx[e.ex], hy = G.hy[e.ey];
     T phis = 0, Q1 = 0;
     if (act) {
@@ -313,7 +321,7 @@ struct MomOut {
 
 template <typename T>
 __global__ void k_momentum(Geo<T> G, Phys<T> q, MomIn<T> in, MomOut<T> out) {
-    PF_ELEM_SMEM(T, G, 6)
+    PF_ELEM_SMEM(T, G, 12)
     // inputs with in-plane derivatives: phi, W, u*_x, u*_y, u*_z, P*
     T *sphi = sF, *sW = sF + pp_, *sux = sF + 2 * pp_, *suy = sF + 3 * pp_, *suz = sF + 4 * pp_,
       *sPs = sF + 5 * pp_;
@@ -322,7 +330,7 @@ __global__ void k_momentum(Geo<T> G, Phys<T> q, MomIn<T> in, MomOut<T> out) {
       *sKz = sF + 10 * pp_, *sJx = sF + 11 * pp_;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
-    const bool act = e.t < pp_;
+    const bool act = e.act;
     const bool d3 = in.un[2] != nullptr;
     const int J = q.J;
     const T hx = G.hx[e.ex], hy = G.hy[e.ey];
@@ -444,7 +452,7 @@ __global__ void k_ugradp(Geo<T> G, Phys<T> q, const T *__restrict__ P, T *__rest
     T *sPv = sF;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
-    const bool act = e.t < pp_;
+    const bool act = e.act;
     if (act) sPv[e.t] = P[e.g];
     __syncthreads();
     if (!act) return;
@@ -528,25 +536,82 @@ struct FwdArgs {
     int tp;                         // nodes per block
 };
 
+// element-local slots (within plane 0) that sum into nodal index q; unused slots are -1
+template <typename T>
+__device__ __forceinline__ void dss_sources(const Geo<T> &G, int q, int src[4]) {
+    const int K = G.K, p = G.p, i = q / G.nx, j = q % G.nx;
+    int eys[2], bs[2], ny_ = 0;
+    if (i % K == 0) {
+        if (i > 0) { eys[ny_] = i / K - 1; bs[ny_++] = K; }
+        if (i < G.ny - 1) { eys[ny_] = i / K; bs[ny_++] = 0; }
+    } else {
+        eys[ny_] = i / K; bs[ny_++] = i % K;
+    }
+    int exs[2], as[2], nx_ = 0;
+    if (j % K == 0) {
+        exs[nx_] = j / K; as[nx_++] = 0;
+        exs[nx_] = (j / K - 1 + G.ex) % G.ex; as[nx_++] = K;
+    } else {
+        exs[nx_] = j / K; as[nx_++] = j % K;
+    }
+    int c = 0;
+    for (int cy = 0; cy < ny_; ++cy)
+        for (int cx = 0; cx < nx_; ++cx) src[c++] = (eys[cy] * G.ex + exs[cx]) * (p * p) + bs[cy] * p + as[cx];
+    for (; c < 4; ++c) src[c] = -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T gather4(const T *__restrict__ L, long long zoff, const int *s) {
+    T v = L[zoff + s[0]];
+    if (s[1] >= 0) v += L[zoff + s[1]];
+    if (s[2] >= 0) v += L[zoff + s[2]];
+    if (s[3] >= 0) v += L[zoff + s[3]];
+    return v;
+}
+
 template <typename T>
 __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
     const int nz = G.nz, ld = nz + 1, tp = a.tp;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    int *ssrc = reinterpret_cast<int *>(buf + tp * ld);   // tp x 4 DSSUM sources
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
     const int q0 = blockIdx.x * tp;
-    for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
-        const int z = idx / tp, ql = idx % tp, qg = q0 + ql;
-        T v0 = 0, v1 = 0;
-        if (qg < G.n2) {
-            const int i = qg / G.nx, j = qg % G.nx;
-            const long long gi = (long long)z * G.n2 + qg;
-            v0 = a.x0_local ? dssum(G, a.X0, z, i, j) : a.X0[gi];
-            if (a.X1) v1 = a.x1_local ? dssum(G, a.X1, z, i, j) : a.X1[gi];
+    for (int ql = threadIdx.x; ql < tp; ql += blockDim.x) {
+        int s[4] = {-1, -1, -1, -1};
+        if (q0 + ql < G.n2) dss_sources(G, q0 + ql, s);
+        for (int c = 0; c < 4; ++c) ssrc[ql * 4 + c] = s[c];
+    }
+    __syncthreads();
+    const long long lplane = (long long)G.ex * G.ey * G.p * G.p;
+    const int total = tp * nz;
+    for (int base = threadIdx.x; base < total; base += 4 * blockDim.x) {
+        T v0[4], v1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {   // four independent gathers in flight
+            const int idx = base + u * blockDim.x;
+            v0[u] = 0;
+            v1[u] = 0;
+            if (idx < total) {
+                const int z = idx / tp, ql = idx - z * tp, qg = q0 + ql;
+                if (qg < G.n2) {
+                    const long long gi = (long long)z * G.n2 + qg;
+                    const int *s = ssrc + ql * 4;
+                    v0[u] = a.x0_local ? gather4(a.X0, z * lplane, s) : a.X0[gi];
+                    if (a.X1) v1[u] = a.x1_local ? gather4(a.X1, z * lplane, s) : a.X1[gi];
+                }
+            }
         }
-        buf[ql * ld + bitrev(z, bits)] = {v0, v1};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < total) {
+                const int z = idx / tp, ql = idx - z * tp;
+                buf[ql * ld + bitrev(z, bits)] = {v0[u], v1[u]};
+            }
+        }
     }
     __syncthreads();
     if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
@@ -741,9 +806,11 @@ struct GemmArgs {
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
-    __shared__ T sA[BK][BM + 1];
-    __shared__ T sB[BK][BN];
-    const int nth = (BM / TM) * (BN / TN);
+    constexpr int NTH = (BM / TM) * (BN / TN);
+    constexpr int LA = BM * BK / NTH;   // A elements staged per thread per k tile
+    constexpr int LB = BK * BN / NTH;
+    __shared__ T sA[2][BK][BM + 1];
+    __shared__ T sB[2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
     const long long m0 = (long long)blockIdx.y * BM;
@@ -753,32 +820,56 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0;
-    for (int k0 = 0; k0 < g.N; k0 += BK) {
-        for (int idx = tid; idx < BM * BK; idx += nth) {
-            const int r = idx / BK, c = idx % BK;
+    T ra_[LA], rb_[LB];
+    auto fetch = [&](int k0) {   // all loads of one k tile issued back to back
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            const int idx = tid + NTH * i, r = idx / BK, c = idx % BK;
             const long long m = m0 + r;
             const int k = k0 + c;
-            sA[c][r] = (m < g.Mrows && k < g.N) ? g.A[m * g.N + k] : T(0);
+            ra_[i] = (m < g.Mrows && k < g.N) ? g.A[m * g.N + k] : T(0);
         }
-        for (int idx = tid; idx < BK * BN; idx += nth) {
-            const int r = idx / BN, c = idx % BN;
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const int idx = tid + NTH * i, r = idx / BN, c = idx % BN;
             const int k = k0 + r, n = n0 + c;
-            sB[r][c] = (k < g.N && n < g.N) ? g.B[(long long)k * g.N + n] : T(0);
+            rb_[i] = (k < g.N && n < g.N) ? g.B[(long long)k * g.N + n] : T(0);
         }
-        __syncthreads();
+    };
+    auto put = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            const int idx = tid + NTH * i;
+            sA[buf][idx % BK][idx / BK] = ra_[i];
+        }
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const int idx = tid + NTH * i;
+            sB[buf][idx / BN][idx % BN] = rb_[i];
+        }
+    };
+    fetch(0);
+    put(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < g.N; k0 += BK) {
+        const bool more = k0 + BK < g.N;
+        if (more) fetch(k0 + BK);          // next tile in flight during this tile's FMAs
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T ra[TM], rb[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) ra[i] = sA[kk][ty * TM + i];
+            for (int i = 0; i < TM; ++i) ra[i] = sA[buf][kk][ty * TM + i];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) rb[j] = sB[kk][tx * TN + j];
+            for (int j = 0; j < TN; ++j) rb[j] = sB[buf][kk][tx * TN + j];
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] += ra[i] * rb[j];
         }
+        if (more) put(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {

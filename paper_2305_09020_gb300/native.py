@@ -19,7 +19,7 @@ from . import _build
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTSEPARABLE, PF_EDIVERGED, PF_ETIMEOUT, PF_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 PF_BC_DIRICHLET, PF_BC_NEUMANN = 0, 1
-PF_FP64, PF_MIXED = 0, 1
+PF_FP64, PF_MIXED, PF_MIXED_SIMT = 0, 1, 2
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64

@@ -33,7 +33,7 @@ def _assert_all(res, tol):
 
 @pytest.mark.parametrize("bcset", [native.PF_BCSET_V, native.PF_BCSET_NN, native.PF_BCSET_P, native.PF_BCSET_U])
 @pytest.mark.parametrize("nz,mode", [(1, 0), (8, 0), (8, 3), (8, 4)])
-@pytest.mark.parametrize("precision", [native.PF_FP64, native.PF_MIXED])
+@pytest.mark.parametrize("precision", [native.PF_FP64, native.PF_MIXED, native.PF_MIXED_SIMT])
 def test_helmholtz_parity(bcset, nz, mode, precision):
     """pf_solve_helmholtz equals the oracle's assembled (K + (lam + beta^2) M) x = M f."""
     wl = workloads.small3d(ex=3, ey=3, order=5, nz=nz) if nz > 1 else workloads.small2d(ex=3, ey=3, order=5)
@@ -113,3 +113,28 @@ def test_mixed_precision_2d_droplet():
 def test_mixed_precision_3d_small():
     wl = workloads.small3d(ex=4, ey=2, order=5, nz=8)
     _assert_mixed(run_pair(wl, 10, precision=native.PF_MIXED, check_every=1), 10)
+
+
+def test_mixed_simt_precision_2d_droplet():
+    """The same bars for the FP32 path whose transforms run on the SIMT pipe."""
+    wl = workloads.droplet2d()
+    _assert_mixed(run_pair(wl, 100, precision=native.PF_MIXED_SIMT, check_every=25), 100)
+
+
+@pytest.mark.parametrize("precision", [native.PF_FP64, native.PF_MIXED])
+def test_graph_replay_is_bit_identical(precision):
+    """Steady steps replayed from the captured CUDA graphs (a non-default stream) give the same
+    bits as eager launches on the legacy stream."""
+    torch = pytest.importorskip("torch")
+    from gpu_util import ALL
+    wl = workloads.small3d(ex=4, ey=2, order=4, nz=8)
+    s = torch.cuda.Stream()
+    a = native.from_workload(wl, precision=precision, stream=s.cuda_stream)
+    b = native.from_workload(wl, precision=precision)
+    a.step(7)
+    b.step(7)
+    fa, fb = a.get(ALL), b.get(ALL)
+    a.close()
+    b.close()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
