@@ -209,6 +209,48 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
  * = {n_x, n_y, Nz, number of real values per field}. */
 int pf_geometry(const pf_handle *h, double *nodes_x, double *nodes_y, int dims[4]);
 
+/* ---- ensembles of independent 2D runs ---------------------------------------------- */
+
+/* Opaque ensemble: nrun independent 2D runs (nz = 1 meshes) advanced together.  Runs that
+ * share the mesh (breakpoints, order), the fluid constants other than eps1/eps2, the kinds of
+ * the potential sides and the scheme are grouped; each group's runs are the planes of one
+ * engine (per-run permittivities and electrode voltages), and one CUDA graph replays a time
+ * step of every group. */
+typedef struct pf_batch pf_batch;
+
+/* meshes/fluids/vbcs: nrun descriptors each (nz must be 1); scheme shared by all runs;
+ * phi0[r]: host array of run r's n_x*n_y initial phase field.  Each group computes its
+ * initial potentials by the fixed point of the Remark in Sec. 3.1 (FP64).  Errors: PF_EINVAL
+ * (message in pf_last_error(NULL)), PF_ENOMEM, PF_ECUDA. */
+int pf_batch_create(int nrun, const pf_mesh *meshes, const pf_fluid *fluids, const pf_vbc *vbcs,
+                    const pf_scheme *scheme, const double *const *phi0, void *cuda_stream, pf_batch **out);
+
+/* Advance every run nsteps time steps (Algorithm 1; BDF1 for the first step). */
+int pf_batch_step(pf_batch *b, int nsteps);
+
+/* Per-run FP64 max |u| (out[nrun]) and phase mass int phi (mass[nrun], nullable); synchronous. */
+int pf_batch_umax(pf_batch *b, double *umax, double *mass);
+
+/* Step until every run has max|u| < tol, checking every check_every steps, or until the
+ * ensemble has taken max_steps steps.  steps_out[r] = the step count at which run r was first
+ * seen below tol, or -1.  Returns PF_EDIVERGED if a run produced a non-finite value. */
+int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_steps, int check_every, int *steps_out);
+
+/* Copy run r's fields to the host; mask and layout as pf_get_fields for one 2D run. */
+int pf_batch_get_fields(pf_batch *b, int run, unsigned mask, double *host_out, size_t n);
+
+/* Autotuner: for every group, time `steps` steps with each transform GEMM variant (tensor
+ * core where the precision has it, SIMT with 32x32 and 64x64 tiles) and keep the fastest.
+ * It advances the ensemble by (number of variants x steps) steps.  ms_out[g] (nullable,
+ * capacity >= number of groups) receives the best time per step of group g; returns the
+ * number of groups (>= 0) or an error code. */
+int pf_batch_autotune(pf_batch *b, int steps, double *ms_out);
+
+/* Number of groups and, per run, its group (group_of[nrun], nullable). */
+int pf_batch_groups(const pf_batch *b, int *group_of);
+
+void pf_batch_destroy(pf_batch *b);
+
 /* ---- allocation-free solve ---------------------------------------------------------- */
 
 /* Capacity, in doubles, of each of the two scratch buffers of pf_fdm_solve_static. */

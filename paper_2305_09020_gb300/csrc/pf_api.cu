@@ -54,6 +54,9 @@ struct HostSetup {
     double rho1, rho2, mu1, mu2, eps1, eps2, sigma, eta, gamma1, theta;
     double dt, S, nu_m, rho0, eps0, lam, cos_theta;
     int bdf, precision;
+    // ensemble of independent 2D runs (batch > 0): per-run permittivities and voltages
+    int batch = 0;
+    std::vector<double> beps1, beps2, bvb, bvt;
 };
 
 double alpha_of(const HostSetup &s, int J) {
@@ -152,6 +155,10 @@ struct Engine {
     T *Ex, *Ey, *W, *dzW, *Lf, *Q2;
     T *LA, *LB, *LAU[3], *LBU[3], *faceU;
     T *RHS, *OUT, *PSIH, *Q2H, *FACEH, *W1, *W2;
+    // ensemble planes (indep): per-plane permittivities, 1/eps0, voltages, lifting columns
+    bool indep = false;
+    T *peps1 = nullptr, *peps2 = nullptr, *peps0 = nullptr, *pscale = nullptr, *pvb = nullptr, *pvt = nullptr;
+    T *liftb = nullptr, *liftt = nullptr;
     double *red;
     int *dev_err;   // device error word (bounded waits)
     int cur = 0;
@@ -165,6 +172,7 @@ struct Engine {
     };
     std::vector<TcB> tcb;
     bool use_tc = false;
+    int simt_tile = 0;   // SIMT GEMM tile: 0 heuristic, 32 or 64 forced (autotuner)
     // steady-state (BDF2) step captured once per history-slot parity; replayed by pf_step
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2][PF_KC_COUNT] = {};
@@ -214,11 +222,13 @@ struct Engine {
     }
 
     Engine(const HostSetup &s, cudaStream_t stream, Prof *pr) : hs(s), prof(pr), st(stream) {
-        ex = s.ex; ey = s.ey; K = s.K; p = s.p; nx = s.nx; ny = s.ny; nz = s.nz;
+        ex = s.ex; ey = s.ey; K = s.K; p = s.p; nx = s.nx; ny = s.ny;
+        indep = s.batch > 0;
+        nz = indep ? s.batch : s.nz;   // planes: Fourier planes, or the runs of an ensemble
         n2 = nx * ny;
         N = (long long)n2 * nz;
         NL = (long long)ex * ey * p * p * nz;
-        d3 = nz > 1;
+        d3 = !indep && nz > 1;
         hx = up(s.hx); hy = up(s.hy); D = up(s.D); Dw = up(s.Dw); w = up(s.w);
         Mx = up(s.Mx); My = up(s.My);
         std::vector<double> tmp;
@@ -237,6 +247,20 @@ struct Engine {
             Ly[b] = up(s.Ly[b]);
         }
         liftV = up(s.liftV);
+        if (indep) {
+            std::vector<double> e0(nz), sc(nz), lb(ny, 0.0), lt(ny, 0.0);
+            for (int q = 0; q < nz; ++q) {
+                e0[q] = std::max(s.beps1[q], s.beps2[q]);
+                sc[q] = 1.0 / e0[q];
+            }
+            peps1 = up(s.beps1); peps2 = up(s.beps2); peps0 = up(e0); pscale = up(sc);
+            pvb = up(s.bvb); pvt = up(s.bvt);
+            for (int i = 0; i < ny; ++i) {
+                if (s.vrow0 >= 0) lb[i] = s.Ky[(size_t)i * ny + 0];
+                if (s.vrow1 >= 0) lt[i] = s.Ky[(size_t)i * ny + (ny - 1)];
+            }
+            liftb = up(lb); liftt = up(lt);
+        }
         {
             std::vector<cplx<T>> h(std::max(1, nz / 2));
             for (int k = 0; k < nz / 2; ++k) {
@@ -252,8 +276,8 @@ struct Engine {
             for (int pl = 0; pl < 3 * nz; ++pl) {
                 const int pp = pl % nz;
                 int k = 0;
-                if (nz > 1) k = (pp == 0) ? 0 : (pp == 1 ? nz / 2 : pp / 2);
-                const double beta = nz > 1 ? 2.0 * M_PI * k / s.lz : 0.0;
+                if (d3) k = (pp == 0) ? 0 : (pp == 1 ? nz / 2 : pp / 2);
+                const double beta = d3 ? 2.0 * M_PI * k / s.lz : 0.0;
                 v[pl] = c + beta * beta;
             }
             return up(v);
@@ -292,7 +316,7 @@ struct Engine {
         faceU = mk<T>((size_t)ex * p * nz);
         RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
-        red = mk<double>(1024);
+        red = mk<double>(std::max<long long>(1024, nz));
         dev_err = mk<int>(1);
         use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED;
         if (use_tc) {
@@ -379,6 +403,7 @@ struct Engine {
         q.nu_m = (T)hs.nu_m; q.dt = (T)hs.dt; q.sigma = (T)hs.sigma; q.cos_theta = (T)hs.cos_theta;
         q.alpha = (T)alpha_of(hs, J); q.gamma0 = (T)(J == 1 ? 1.0 : 1.5); q.J = J;
         q.wetting = std::fabs(hs.cos_theta) > 1e-15 ? 1 : 0;
+        q.eps1_p = peps1; q.eps2_p = peps2; q.eps0_p = peps0;
         return q;
     }
 
@@ -429,7 +454,8 @@ struct Engine {
         constexpr int BK = sizeof(T) == 8 ? 8 : 16;
         const long long tiles64 = ((Ncol + 63) / 64) * ((Mrows + 63) / 64);
         prof->begin(PF_KC_GEMM, st);
-        if (tiles64 >= 4 * 152 && Ncol % 64 > 32) {
+        const bool big = simt_tile == 64 || (simt_tile == 0 && tiles64 >= 4 * 152 && Ncol % 64 > 32);
+        if (big) {
             dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 63) / 64));
             pf::k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(g);
         } else {
@@ -489,6 +515,28 @@ struct Engine {
         prof->end(st);
     }
 
+    void fwd_indep(const T *X0, const T *X1, const T *scale_p, bool lift, T *out, T *out1) {
+        pf::IndepFwd<T> a{X0, X1, scale_p, lift ? liftb : nullptr, lift ? liftt : nullptr, pvb, pvt, out, out1};
+        prof->begin(PF_KC_FWD, st);
+        pf::k_fwd_indep<T><<<dim3((n2 + 255) / 256, nz), 256, 0, st>>>(geo(), a);
+        check_launch();
+        prof->end(st);
+    }
+    void inv_indep(const T *Y, T *out, bool dirichlet_v, bool phi_variant, double alpha) {
+        pf::IndepInv<T> a{};
+        a.Y = Y; a.out = out;
+        a.drow0 = dirichlet_v ? hs.vrow0 : -1; a.drow1 = dirichlet_v ? hs.vrow1 : -1;
+        a.v0_p = pvb; a.v1_p = pvt;
+        if (phi_variant) {
+            a.psi = PSIH; a.Q2n = Q2; a.alpha = (T)alpha; a.S_eta2 = (T)(hs.S / std::pow(hs.eta, 2.0));
+            a.outW = W; a.outL = Lf;
+        }
+        prof->begin(PF_KC_INV, st);
+        pf::k_inv_indep<T><<<dim3((n2 + 255) / 256, nz), 256, 0, st>>>(geo(), a);
+        check_launch();
+        prof->end(st);
+    }
+
     // ---- the potential sub-step (also used by the initial fixed point) ----------------------
     void potential(int J, const T *phin, const T *phio, const T *Vn, const T *Vo, const T *Ezn, const T *Ezo,
                    T *Vout, T *Ezout) {
@@ -499,9 +547,11 @@ struct Engine {
                                                                             Ezo, LA, d3 ? LB : nullptr);
         check_launch();
         prof->end(st);
-        fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
+        if (indep) fwd_indep(LA, nullptr, pscale, true, RHS, nullptr);
+        else fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_V, shV, nz);
-        inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
+        if (indep) inv_indep(OUT, Vout, true, false, 0.0);
+        else inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
     }
 
     void efield(const T *Vf) {
@@ -528,11 +578,18 @@ struct Engine {
             Ey, Ez[o], LA, Q2, q.wetting ? faceU : nullptr);
         check_launch();
         prof->end(st);
-        fwd(LA, 1, Q2, 0, 1, 1.0, nullptr, RHS, Q2H);
+        if (indep) fwd_indep(LA, Q2, nullptr, false, RHS, Q2H);
+        else fwd(LA, 1, Q2, 0, 1, 1.0, nullptr, RHS, Q2H);
         fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz);
         // phi^{n+1}
         const T *faceh = nullptr;
-        if (q.wetting) {
+        if (q.wetting && indep) {
+            prof->begin(PF_KC_OTHER, st);
+            pf::k_face_indep<T><<<dim3((nx + 127) / 128, nz), 128, 0, st>>>(G, faceU, FACEH);
+            check_launch();
+            prof->end(st);
+            faceh = FACEH;
+        } else if (q.wetting) {
             const int tp = fwd_tp();
             const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + tp * (nz + 1)) * sizeof(cplx<T>);
             prof->begin(PF_KC_OTHER, st);
@@ -546,7 +603,8 @@ struct Engine {
         check_launch();
         prof->end(st);
         fdm(RHS, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
-        inv_phi(al, phi[o], dzphi[o]);
+        if (indep) inv_indep(OUT, phi[o], false, true, al);
+        else inv_phi(al, phi[o], dzphi[o]);
         // P^{n+1}
         pf::MomIn<T> mi;
         mi.phi = phi[o]; mi.dzphi = dzphi[o]; mi.W = W; mi.dzW = dzW; mi.L = Lf;
@@ -562,9 +620,11 @@ struct Engine {
         pf::k_momentum<T><<<elem_grid(), elem_threads(), elem_smem(12), st>>>(G, q, mi, mo);
         check_launch();
         prof->end(st);
-        fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr);
+        if (indep) fwd_indep(LA, nullptr, nullptr, false, RHS, nullptr);
+        else fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_P, shP, nz);
-        inv(OUT, P[o], dzP[o], -1, 0.0, -1, 0.0);
+        if (indep) inv_indep(OUT, P[o], false, false, 0.0);
+        else inv(OUT, P[o], dzP[o], -1, 0.0, -1, 0.0);
         // u^{n+1}
         prof->begin(PF_KC_UGRADP, st);
         pf::k_ugradp<T><<<elem_grid(), elem_threads(), elem_smem(1), st>>>(G, q, P[o], LAU[0], LAU[1],
@@ -572,10 +632,24 @@ struct Engine {
         check_launch();
         prof->end(st);
         const int dc = d3 ? 3 : 2;
-        for (int c = 0; c < dc; ++c) fwd(LAU[c], 1, d3 ? LBU[c] : nullptr, 1, 0, 1.0, nullptr, RHS + c * N, nullptr);
+        for (int c = 0; c < dc; ++c) {
+            if (indep) fwd_indep(LAU[c], nullptr, nullptr, false, RHS + c * N, nullptr);
+            else fwd(LAU[c], 1, d3 ? LBU[c] : nullptr, 1, 0, 1.0, nullptr, RHS + c * N, nullptr);
+        }
         fdm(RHS, OUT, PF_BCSET_U, shU[J - 1], dc * nz);
-        for (int c = 0; c < dc; ++c) inv(OUT + c * N, u[c][o], dzu[c][o], -1, 0.0, -1, 0.0);
+        for (int c = 0; c < dc; ++c) {
+            if (indep) inv_indep(OUT + c * N, u[c][o], false, false, 0.0);
+            else inv(OUT + c * N, u[c][o], dzu[c][o], -1, 0.0, -1, 0.0);
+        }
         cur = o;
+    }
+
+    // per-plane FP64 reduction (kind 0: sum of M x, kind 1: max |x|) of level-n field x into host out[nz]
+    void reduce_planes(const T *x, int kind, double *out) {
+        pf::k_reduce_planes<T><<<nz, 256, 0, st>>>(x, Mx, My, nx, n2, kind, red);
+        check_launch();
+        PF_CU(cudaMemcpyAsync(out, red, nz * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PF_CU(cudaStreamSynchronize(st));
     }
 
     // ---- reductions (FP64 accumulation) -------------------------------------------------------
@@ -683,12 +757,15 @@ void build_setup(HostSetup &s) {
 // initial potential: fixed point of the Remark in Sec. 3.1 in FP64, run to the round-off
 // floor: stop when the max-norm update is <= 1e-15 vmax, or once it is below 1e-11 vmax and
 // no longer decreases, or after 20000 iterations (vmax = max(1, |electrode voltages|)).
-int initial_potential(pf_handle *h, Engine<double> &E, const double *phi0_dev) {
+int initial_potential(const HostSetup &hs, Engine<double> &E, const double *phi0_dev, int &v_iters,
+                      std::string &err) {
     const double tol = 1e-15;
     double prev = INFINITY;
     double vmax = 1.0;
-    if (h->hs.vrow0 >= 0) vmax = std::max(vmax, std::fabs(h->hs.v0));
-    if (h->hs.vrow1 >= 0) vmax = std::max(vmax, std::fabs(h->hs.v1));
+    if (hs.vrow0 >= 0) vmax = std::max(vmax, std::fabs(hs.v0));
+    if (hs.vrow1 >= 0) vmax = std::max(vmax, std::fabs(hs.v1));
+    for (double v : hs.bvb) vmax = std::max(vmax, std::fabs(v));
+    for (double v : hs.bvt) vmax = std::max(vmax, std::fabs(v));
     int a = 0;   // slot of the current iterate
     PF_CU(cudaMemsetAsync(E.V[0], 0, E.N * sizeof(double), E.st));
     if (E.d3) PF_CU(cudaMemsetAsync(E.Ez[0], 0, E.N * sizeof(double), E.st));
@@ -697,11 +774,14 @@ int initial_potential(pf_handle *h, Engine<double> &E, const double *phi0_dev) {
         E.potential(1, phi0_dev, phi0_dev, E.V[a], E.V[a], E.Ez[a], E.Ez[a], E.V[1 - a], E.Ez[1 - a]);
         const double diff = E.reduce(E.V[1 - a], E.V[a], 2);
         a = 1 - a;
-        if (!(diff == diff)) return fail(h, PF_EDIVERGED, "non-finite value in the initial potential");
+        if (!(diff == diff)) {
+            err = "non-finite value in the initial potential";
+            return PF_EDIVERGED;
+        }
         if (diff <= tol * vmax || (diff <= 1e-11 * vmax && diff >= prev)) break;
         prev = diff;
     }
-    h->v_iters = std::min(it, 20000);
+    v_iters = std::min(it, 20000);
     if (a != 0) {
         PF_CU(cudaMemcpyAsync(E.V[0], E.V[1], E.N * sizeof(double), cudaMemcpyDeviceToDevice, E.st));
         if (E.d3) PF_CU(cudaMemcpyAsync(E.Ez[0], E.Ez[1], E.N * sizeof(double), cudaMemcpyDeviceToDevice, E.st));
@@ -751,7 +831,7 @@ void dz_of(Engine<T> &E, const T *x, T *dzx) {
 }
 
 template <typename T>
-int engine_init_state(pf_handle *h, Engine<T> &E, const double *phi0, const double *u0) {
+int engine_init_state(Engine<T> &E, const double *phi0, const double *u0) {
     upload_field(E, E.phi[0], phi0);
     dz_of(E, E.phi[0], E.dzphi[0]);
     if (u0) {
@@ -780,34 +860,34 @@ int do_steps(pf_handle *h, Engine<T> &E, int nsteps) {
 }  // namespace
 
 // ============================================================================================
-extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, const pf_scheme *scheme,
-                         const double *phi0, const double *u0, void *cuda_stream, pf_handle **out) {
-    if (out) *out = nullptr;
-    if (!mesh || !fluid || !vbc || !scheme || !phi0 || !out) return fail(nullptr, PF_EINVAL, "null argument");
-    if (mesh->ex < 1 || mesh->ey < 1 || !mesh->xb || !mesh->yb) return fail(nullptr, PF_EINVAL, "bad element counts");
-    if (mesh->order < 2 || mesh->order > 15) return fail(nullptr, PF_EINVAL, "order must be in [2, 15]");
+namespace {
+
+// Validate the descriptors and fill the host constants (Sec. 2.1, Sec. 3.1); no device work.
+int fill_setup(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, const pf_scheme *scheme,
+               HostSetup &s, std::string &err) {
+    auto bad = [&](const char *m) { err = m; return PF_EINVAL; };
+    if (!mesh || !fluid || !vbc || !scheme) return bad("null argument");
+    if (mesh->ex < 1 || mesh->ey < 1 || !mesh->xb || !mesh->yb) return bad("bad element counts");
+    if (mesh->order < 2 || mesh->order > 15) return bad("order must be in [2, 15]");
     if (mesh->nz < 1 || (mesh->nz > 1 && ((mesh->nz & (mesh->nz - 1)) != 0 || mesh->nz > 1024)))
-        return fail(nullptr, PF_EINVAL, "nz must be 1 or a power of two <= 1024");
-    if (mesh->nz > 1 && !(mesh->lz > 0)) return fail(nullptr, PF_EINVAL, "lz must be positive");
-    if (mesh->ex * mesh->order < 2) return fail(nullptr, PF_EINVAL, "need at least 2 nodes in x");
+        return bad("nz must be 1 or a power of two <= 1024");
+    if (mesh->nz > 1 && !(mesh->lz > 0)) return bad("lz must be positive");
+    if (mesh->ex * mesh->order < 2) return bad("need at least 2 nodes in x");
     for (int e = 0; e < mesh->ex; ++e)
-        if (!(mesh->xb[e + 1] > mesh->xb[e])) return fail(nullptr, PF_EINVAL, "xb must increase");
+        if (!(mesh->xb[e + 1] > mesh->xb[e])) return bad("xb must increase");
     for (int e = 0; e < mesh->ey; ++e)
-        if (!(mesh->yb[e + 1] > mesh->yb[e])) return fail(nullptr, PF_EINVAL, "yb must increase");
-    if (vbc->bottom_kind != PF_BC_DIRICHLET && vbc->bottom_kind != PF_BC_NEUMANN) return fail(nullptr, PF_EINVAL, "bad bottom_kind");
-    if (vbc->top_kind != PF_BC_DIRICHLET && vbc->top_kind != PF_BC_NEUMANN) return fail(nullptr, PF_EINVAL, "bad top_kind");
+        if (!(mesh->yb[e + 1] > mesh->yb[e])) return bad("yb must increase");
+    if (vbc->bottom_kind != PF_BC_DIRICHLET && vbc->bottom_kind != PF_BC_NEUMANN) return bad("bad bottom_kind");
+    if (vbc->top_kind != PF_BC_DIRICHLET && vbc->top_kind != PF_BC_NEUMANN) return bad("bad top_kind");
     if (vbc->bottom_kind == PF_BC_NEUMANN && vbc->top_kind == PF_BC_NEUMANN)
-        return fail(nullptr, PF_EINVAL, "the potential needs an electrode (Dirichlet) on at least one side");
+        return bad("the potential needs an electrode (Dirichlet) on at least one side");
     const pf_fluid &f = *fluid;
     if (!(f.rho1 > 0 && f.rho2 > 0 && f.mu1 > 0 && f.mu2 > 0 && f.eps1 > 0 && f.eps2 > 0 && f.sigma >= 0 &&
           f.eta > 0 && f.gamma1 > 0))
-        return fail(nullptr, PF_EINVAL, "fluid parameters must be positive");
-    if (!(scheme->dt > 0) || (scheme->bdf != 1 && scheme->bdf != 2)) return fail(nullptr, PF_EINVAL, "bad dt or bdf");
+        return bad("fluid parameters must be positive");
+    if (!(scheme->dt > 0) || (scheme->bdf != 1 && scheme->bdf != 2)) return bad("bad dt or bdf");
     if (scheme->precision != PF_FP64 && scheme->precision != PF_MIXED && scheme->precision != PF_MIXED_SIMT)
-        return fail(nullptr, PF_EINVAL, "bad precision");
-
-    std::unique_ptr<pf_handle> h(new pf_handle());
-    HostSetup &s = h->hs;
+        return bad("bad precision");
     s.ex = mesh->ex; s.ey = mesh->ey; s.K = mesh->order; s.nz = mesh->nz; s.lz = mesh->nz > 1 ? mesh->lz : 1.0;
     s.xb.assign(mesh->xb, mesh->xb + s.ex + 1);
     s.yb.assign(mesh->yb, mesh->yb + s.ey + 1);
@@ -827,36 +907,58 @@ extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vb
     s.cos_theta = std::cos(s.theta * M_PI / 180.0);
     if (vbc->bottom_kind == PF_BC_DIRICHLET) { s.vrow0 = 0; s.v0 = vbc->v_bottom; }
     if (vbc->top_kind == PF_BC_DIRICHLET) { s.vrow1 = s.ey * s.K; s.v1 = vbc->v_top; }
-    build_setup(s);
+    return PF_OK;
+}
+
+// Device state for a filled set-up: initial state, V^0 (FP64), E^0, both history levels,
+// then the working-precision engine.  Returns a PF_* code (CUDA errors are thrown).
+int build_engines(const HostSetup &s, const double *phi0, const double *u0, cudaStream_t st, Prof *prof,
+                  std::unique_ptr<Engine<double>> &e64out, std::unique_ptr<Engine<float>> &e32out, int &v_iters,
+                  std::string &err) {
+    std::unique_ptr<Engine<double>> e64(new Engine<double>(s, st, prof));
+    engine_init_state(*e64, phi0, u0);
+    const int rc = initial_potential(s, *e64, e64->phi[0], v_iters, err);
+    if (rc != PF_OK) return rc;
+    e64->efield(e64->V[0]);
+    copy_level(*e64, 0, 1);
+    e64->cur = 0;
+    if (s.precision == PF_FP64) {
+        e64out = std::move(e64);
+        return PF_OK;
+    }
+    std::unique_ptr<Engine<float>> e32(new Engine<float>(s, st, prof));
+    auto cv = [&](const double *src, float *dst) {
+        if (!src || !dst) return;
+        pf::k_convert<double, float><<<1024, 256, 0, st>>>(src, dst, e64->N);
+    };
+    for (int l = 0; l < 2; ++l) {
+        cv(e64->V[l], e32->V[l]); cv(e64->Ez[l], e32->Ez[l]); cv(e64->phi[l], e32->phi[l]);
+        cv(e64->dzphi[l], e32->dzphi[l]); cv(e64->P[l], e32->P[l]); cv(e64->dzP[l], e32->dzP[l]);
+        for (int c = 0; c < 3; ++c) { cv(e64->u[c][l], e32->u[c][l]); cv(e64->dzu[c][l], e32->dzu[c][l]); }
+    }
+    cv(e64->Ex, e32->Ex); cv(e64->Ey, e32->Ey);
+    PF_CU(cudaGetLastError());
+    PF_CU(cudaStreamSynchronize(st));
+    e64.reset();
+    e32out = std::move(e32);
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, const pf_scheme *scheme,
+                         const double *phi0, const double *u0, void *cuda_stream, pf_handle **out) {
+    if (out) *out = nullptr;
+    if (!phi0 || !out) return fail(nullptr, PF_EINVAL, "null argument");
+    std::unique_ptr<pf_handle> h(new pf_handle());
+    std::string err;
+    int rc = fill_setup(mesh, fluid, vbc, scheme, h->hs, err);
+    if (rc != PF_OK) return fail(nullptr, rc, err);
+    build_setup(h->hs);
     h->st = (cudaStream_t)cuda_stream;
     try {
-        // the initial potential always runs in FP64
-        std::unique_ptr<Engine<double>> e64(new Engine<double>(s, h->st, &h->prof));
-        engine_init_state(h.get(), *e64, phi0, u0);
-        int rc = initial_potential(h.get(), *e64, e64->phi[0]);
-        if (rc != PF_OK) { g_create_error = h->err; return rc; }
-        e64->efield(e64->V[0]);
-        copy_level(*e64, 0, 1);
-        e64->cur = 0;
-        if (s.precision == PF_FP64) {
-            h->e64 = std::move(e64);
-        } else {
-            std::unique_ptr<Engine<float>> e32(new Engine<float>(s, h->st, &h->prof));
-            auto cv = [&](const double *src, float *dst) {
-                if (!src || !dst) return;
-                pf::k_convert<double, float><<<1024, 256, 0, h->st>>>(src, dst, e64->N);
-            };
-            for (int l = 0; l < 2; ++l) {
-                cv(e64->V[l], e32->V[l]); cv(e64->Ez[l], e32->Ez[l]); cv(e64->phi[l], e32->phi[l]);
-                cv(e64->dzphi[l], e32->dzphi[l]); cv(e64->P[l], e32->P[l]); cv(e64->dzP[l], e32->dzP[l]);
-                for (int c = 0; c < 3; ++c) { cv(e64->u[c][l], e32->u[c][l]); cv(e64->dzu[c][l], e32->dzu[c][l]); }
-            }
-            cv(e64->Ex, e32->Ex); cv(e64->Ey, e32->Ey);
-            PF_CU(cudaGetLastError());
-            PF_CU(cudaStreamSynchronize(h->st));
-            e64.reset();
-            h->e32 = std::move(e32);
-        }
+        rc = build_engines(h->hs, phi0, u0, h->st, &h->prof, h->e64, h->e32, h->v_iters, err);
+        if (rc != PF_OK) return fail(nullptr, rc, err);
     } catch (const CudaError &e) {
         g_create_error = e.where + ": " + cudaGetErrorString(e.code);
         return e.code == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
@@ -1113,4 +1215,336 @@ extern "C" void pf_destroy(pf_handle *h) {
 extern "C" const char *pf_last_error(const pf_handle *h) {
     if (!h) return g_create_error.c_str();
     return h->err.c_str();
+}
+
+// ============================================================================================
+// Ensembles of independent 2D runs
+struct pf_batch {
+    struct Group {
+        HostSetup hs;
+        Prof prof;
+        std::unique_ptr<Engine<double>> e64;
+        std::unique_ptr<Engine<float>> e32;
+        std::vector<int> runs;
+        int v_iters = 0;
+    };
+    std::vector<std::unique_ptr<Group>> groups;
+    std::vector<std::pair<int, int>> where;   // run -> (group, plane)
+    cudaStream_t st = nullptr;
+    long long nstep = 0;
+    int bdf = 2;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<std::vector<long long>> gcounts[2];   // per-group launches of one replayed step
+    std::string err;
+    ~pf_batch() {
+        for (int c = 0; c < 2; ++c)
+            if (graph[c]) cudaGraphExecDestroy(graph[c]);
+    }
+};
+
+namespace {
+
+bool same_group(const HostSetup &a, const HostSetup &b) {
+    return a.ex == b.ex && a.ey == b.ey && a.K == b.K && a.xb == b.xb && a.yb == b.yb && a.rho1 == b.rho1 &&
+           a.rho2 == b.rho2 && a.mu1 == b.mu1 && a.mu2 == b.mu2 && a.sigma == b.sigma && a.eta == b.eta &&
+           a.gamma1 == b.gamma1 && a.theta == b.theta && a.vrow0 == b.vrow0 && a.vrow1 == b.vrow1 &&
+           a.dt == b.dt && a.bdf == b.bdf && a.precision == b.precision && a.S == b.S && a.nu_m == b.nu_m &&
+           a.rho0 == b.rho0;
+}
+
+template <typename F>
+void for_engine(pf_batch::Group &g, F f) {
+    if (g.e64) f(*g.e64);
+    else f(*g.e32);
+}
+
+std::vector<std::vector<long long>> &graph_counts(pf_batch *b, int c) { return b->gcounts[c]; }
+
+int batch_fail(pf_batch *b, int code, const std::string &m) {
+    b->err = m;
+    return code;
+}
+
+void batch_invalidate_graphs(pf_batch *b) {
+    for (int c = 0; c < 2; ++c)
+        if (b->graph[c]) {
+            cudaGraphExecDestroy(b->graph[c]);
+            b->graph[c] = nullptr;
+        }
+}
+
+void batch_step_once(pf_batch *b) {
+    const int J = (b->nstep == 0 || b->bdf == 1) ? 1 : 2;
+    if (J == 1 || b->st == nullptr) {
+        for (auto &g : b->groups) for_engine(*g, [&](auto &E) { E.step(J); });
+    } else {
+        int c = 0;
+        for_engine(*b->groups[0], [&](auto &E) { c = E.cur; });
+        if (!b->graph[c]) {
+            cudaGraph_t gr = nullptr;
+            std::vector<std::vector<long long>> before;
+            for (auto &g : b->groups) before.emplace_back(g->prof.launches, g->prof.launches + PF_KC_COUNT);
+            PF_CU(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+            try {
+                for (auto &g : b->groups) for_engine(*g, [&](auto &E) { E.step(2); });
+            } catch (...) {
+                cudaStreamEndCapture(b->st, &gr);
+                if (gr) cudaGraphDestroy(gr);
+                throw;
+            }
+            PF_CU(cudaStreamEndCapture(b->st, &gr));
+            cudaError_t e = cudaGraphInstantiate(&b->graph[c], gr, 0);
+            cudaGraphDestroy(gr);
+            PF_CU(e);
+            // the capture ran nothing: restore the slots and the counters
+            for (size_t i = 0; i < b->groups.size(); ++i) {
+                auto &g = *b->groups[i];
+                for_engine(g, [&](auto &E) { E.cur = c; });
+                for (int k = 0; k < PF_KC_COUNT; ++k) {
+                    const long long d = g.prof.launches[k] - before[i][k];
+                    g.prof.launches[k] = before[i][k];
+                    before[i][k] = d;   // per-step launches of this group
+                }
+            }
+            // remember the per-step launch counts in the first group's graph slot via a side table
+            b->err.clear();
+            graph_counts(b, c) = before;
+        }
+        PF_CU(cudaGraphLaunch(b->graph[c], b->st));
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            auto &g = *b->groups[i];
+            for (int k = 0; k < PF_KC_COUNT; ++k) g.prof.launches[k] += graph_counts(b, c)[i][k];
+            for_engine(g, [&](auto &E) { E.cur = 1 - c; });
+        }
+    }
+    b->nstep += 1;
+}
+
+}  // namespace
+
+extern "C" int pf_batch_create(int nrun, const pf_mesh *meshes, const pf_fluid *fluids, const pf_vbc *vbcs,
+                               const pf_scheme *scheme, const double *const *phi0, void *cuda_stream,
+                               pf_batch **out) {
+    if (out) *out = nullptr;
+    if (nrun < 1 || !meshes || !fluids || !vbcs || !scheme || !phi0 || !out)
+        return fail(nullptr, PF_EINVAL, "pf_batch_create: null argument or nrun < 1");
+    std::unique_ptr<pf_batch> b(new pf_batch());
+    b->st = (cudaStream_t)cuda_stream;
+    b->bdf = scheme->bdf;
+    b->where.resize(nrun);
+    std::vector<HostSetup> setups(nrun);
+    for (int r = 0; r < nrun; ++r) {
+        std::string err;
+        const int rc = fill_setup(&meshes[r], &fluids[r], &vbcs[r], scheme, setups[r], err);
+        if (rc != PF_OK) return fail(nullptr, rc, "run " + std::to_string(r) + ": " + err);
+        if (meshes[r].nz != 1) return fail(nullptr, PF_EINVAL, "ensemble runs must be 2D (nz = 1)");
+        if (!phi0[r]) return fail(nullptr, PF_EINVAL, "null phi0 of run " + std::to_string(r));
+    }
+    for (int r = 0; r < nrun; ++r) {
+        int gi = -1;
+        for (size_t g = 0; g < b->groups.size(); ++g)
+            if (same_group(b->groups[g]->hs, setups[r])) { gi = (int)g; break; }
+        if (gi < 0) {
+            b->groups.emplace_back(new pf_batch::Group());
+            b->groups.back()->hs = setups[r];
+            gi = (int)b->groups.size() - 1;
+        }
+        auto &g = *b->groups[gi];
+        b->where[r] = {gi, (int)g.runs.size()};
+        g.runs.push_back(r);
+        g.hs.beps1.push_back(setups[r].eps1);
+        g.hs.beps2.push_back(setups[r].eps2);
+        g.hs.bvb.push_back(setups[r].v0);
+        g.hs.bvt.push_back(setups[r].v1);
+    }
+    try {
+        for (auto &gp : b->groups) {
+            auto &g = *gp;
+            g.hs.batch = (int)g.runs.size();
+            build_setup(g.hs);
+            const size_t n2 = (size_t)g.hs.nx * g.hs.ny;
+            std::vector<double> phi(n2 * g.runs.size());
+            for (size_t i = 0; i < g.runs.size(); ++i) std::copy(phi0[g.runs[i]], phi0[g.runs[i]] + n2, phi.begin() + i * n2);
+            std::string err;
+            const int rc = build_engines(g.hs, phi.data(), nullptr, b->st, &g.prof, g.e64, g.e32, g.v_iters, err);
+            if (rc != PF_OK) return fail(nullptr, rc, err);
+        }
+    } catch (const CudaError &e) {
+        g_create_error = e.where + ": " + cudaGetErrorString(e.code);
+        return e.code == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
+    }
+    *out = b.release();
+    return PF_OK;
+}
+
+extern "C" int pf_batch_step(pf_batch *b, int nsteps) {
+    if (!b || nsteps < 0) return PF_EINVAL;
+    try {
+        for (int s = 0; s < nsteps; ++s) batch_step_once(b);
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_batch_umax(pf_batch *b, double *umax, double *mass) {
+    if (!b || !umax) return PF_EINVAL;
+    try {
+        for (auto &gp : b->groups) {
+            auto &g = *gp;
+            const int B = (int)g.runs.size();
+            std::vector<double> um(B, 0.0), t(B), m(B);
+            for_engine(g, [&](auto &E) {
+                for (int c = 0; c < 2; ++c) {
+                    E.reduce_planes(E.u[c][E.cur], 1, t.data());
+                    for (int i = 0; i < B; ++i) um[i] = (t[i] != t[i] || um[i] != um[i]) ? NAN : std::max(um[i], t[i]);
+                }
+                if (mass) E.reduce_planes(E.phi[E.cur], 0, m.data());
+            });
+            for (int i = 0; i < B; ++i) {
+                umax[g.runs[i]] = um[i];
+                if (mass) mass[g.runs[i]] = m[i];
+            }
+        }
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_steps, int check_every, int *steps_out) {
+    if (!b || !steps_out || check_every < 1 || max_steps < 0) return PF_EINVAL;
+    const int nrun = (int)b->where.size();
+    std::vector<double> um(nrun);
+    for (int r = 0; r < nrun; ++r) steps_out[r] = -1;
+    int left = nrun;
+    while (left > 0 && b->nstep < max_steps) {
+        const int n = (int)std::min<long long>(check_every, max_steps - b->nstep);
+        int rc = pf_batch_step(b, n);
+        if (rc != PF_OK) return rc;
+        rc = pf_batch_umax(b, um.data(), nullptr);
+        if (rc != PF_OK) return rc;
+        for (int r = 0; r < nrun; ++r) {
+            if (!(um[r] == um[r])) return batch_fail(b, PF_EDIVERGED, "non-finite velocity in run " + std::to_string(r));
+            if (steps_out[r] < 0 && um[r] < tol) {
+                steps_out[r] = (int)b->nstep;
+                --left;
+            }
+        }
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_batch_get_fields(pf_batch *b, int run, unsigned mask, double *host_out, size_t n) {
+    if (!b || !host_out || run < 0 || run >= (int)b->where.size()) return PF_EINVAL;
+    auto &g = *b->groups[b->where[run].first];
+    const int pl = b->where[run].second;
+    const size_t n2 = (size_t)g.hs.nx * g.hs.ny;
+    size_t need = 0;
+    if (mask & PF_FIELD_V) need += 1;
+    if (mask & PF_FIELD_E) need += 3;
+    if (mask & PF_FIELD_PHI) need += 1;
+    if (mask & PF_FIELD_PSI) need += 1;
+    if (mask & PF_FIELD_P) need += 1;
+    if (mask & PF_FIELD_U) need += 3;
+    if (need * n2 > n) return batch_fail(b, PF_EINVAL, "output buffer too small");
+    try {
+        for_engine(g, [&](auto &E) {
+            using T = typename std::remove_reference<decltype(*E.V[0])>::type;
+            PF_CU(cudaStreamSynchronize(E.st));
+            const int l = (mask & PF_FIELD_OLD) ? 1 - E.cur : E.cur;
+            double *o = host_out;
+            std::vector<T> tmp(n2);
+            auto put = [&](const T *src) {
+                if (src) {
+                    PF_CU(cudaMemcpy(tmp.data(), src + (size_t)pl * n2, n2 * sizeof(T), cudaMemcpyDeviceToHost));
+                    for (size_t i = 0; i < n2; ++i) o[i] = (double)tmp[i];
+                } else {
+                    std::fill(o, o + n2, 0.0);
+                }
+                o += n2;
+            };
+            if (mask & PF_FIELD_V) put(E.V[l]);
+            if (mask & PF_FIELD_E) { put(E.Ex); put(E.Ey); put(nullptr); }
+            if (mask & PF_FIELD_PHI) put(E.phi[l]);
+            if (mask & PF_FIELD_PSI) {
+                std::vector<T> ph(n2);
+                PF_CU(cudaMemcpy(ph.data(), E.phi[E.cur] + (size_t)pl * n2, n2 * sizeof(T), cudaMemcpyDeviceToHost));
+                put(E.Lf);
+                const double al = alpha_of(g.hs, (b->nstep <= 1 || g.hs.bdf == 1) ? 1 : 2);
+                for (size_t i = 0; i < n2; ++i) o[(ptrdiff_t)i - (ptrdiff_t)n2] += al * (double)ph[i];
+            }
+            if (mask & PF_FIELD_P) put(E.P[l]);
+            if (mask & PF_FIELD_U) { put(E.u[0][l]); put(E.u[1][l]); put(nullptr); }
+        });
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
+    if (!b || steps < 1) return PF_EINVAL;
+    try {
+        // make sure the timed steps are steady (BDF2) steps
+        if (b->nstep < 1) batch_step_once(b);
+        cudaEvent_t e0, e1;
+        PF_CU(cudaEventCreate(&e0));
+        PF_CU(cudaEventCreate(&e1));
+        // every group takes the same number of steps (3 variants x (steps + 1), rounded up to an
+        // even count so the history-slot parity of all groups stays equal)
+        int total = 3 * (steps + 1);
+        if (total % 2) total += 1;
+        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+            auto &g = *b->groups[gi];
+            double best = INFINITY;
+            for_engine(g, [&](auto &E) {
+                struct Cand { bool tc; int tile; };
+                std::vector<Cand> cands;
+                if (!E.tcb.empty()) cands.push_back({true, 0});
+                cands.push_back({false, 32});
+                cands.push_back({false, 64});
+                Cand pick = cands[0];
+                int taken = 0;
+                for (const Cand &c : cands) {
+                    E.use_tc = c.tc;
+                    E.simt_tile = c.tile;
+                    E.step(2);   // warm-up of this variant
+                    PF_CU(cudaEventRecord(e0, E.st));
+                    for (int s = 0; s < steps; ++s) E.step(2);
+                    PF_CU(cudaEventRecord(e1, E.st));
+                    PF_CU(cudaEventSynchronize(e1));
+                    taken += steps + 1;
+                    float ms = 0.f;
+                    PF_CU(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms / steps < best) { best = ms / steps; pick = c; }
+                }
+                E.use_tc = pick.tc;
+                E.simt_tile = pick.tile;
+                for (; taken < total; ++taken) E.step(2);
+            });
+            if (ms_out) ms_out[gi] = best;
+        }
+        b->nstep += total;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        batch_invalidate_graphs(b);
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return (int)b->groups.size();
+}
+
+extern "C" int pf_batch_groups(const pf_batch *b, int *group_of) {
+    if (!b) return PF_EINVAL;
+    if (group_of)
+        for (size_t r = 0; r < b->where.size(); ++r) group_of[r] = b->where[r].first;
+    return (int)b->groups.size();
+}
+
+extern "C" void pf_batch_destroy(pf_batch *b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    else cudaDeviceSynchronize();
+    delete b;
 }

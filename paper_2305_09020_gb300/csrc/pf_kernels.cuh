@@ -58,7 +58,20 @@ struct Phys {
     T alpha, gamma0;
     int J;
     int wetting;   // theta_s != 90 degrees
+    const T *eps1_p, *eps2_p, *eps0_p;   // per-plane permittivities of an ensemble (nullable)
 };
+
+// an ensemble plane (blockIdx.y) may carry its own permittivities
+template <typename T>
+__device__ __forceinline__ Phys<T> plane_phys(const Phys<T> &q) {
+    Phys<T> r = q;
+    if (q.eps1_p) {
+        r.eps1 = q.eps1_p[blockIdx.y];
+        r.eps2 = q.eps2_p[blockIdx.y];
+        r.eps0 = q.eps0_p[blockIdx.y];
+    }
+    return r;
+}
 
 // ---- mixture laws (eq. interpolation) and free-energy pieces (Sec. 2.1) -------------------
 template <typename T> __device__ __forceinline__ T rho_of(const Phys<T> &q, T phi) {
@@ -165,10 +178,11 @@ __device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, i
 // A = -int R_2D . grad_2D w  (element-local contributions),  B = int R_z w  (iB multiplier)
 // with R = (eps(phi*) - eps0) grad V*.
 template <typename T>
-__global__ void k_potential(Geo<T> G, Phys<T> q, const T *__restrict__ phin, const T *__restrict__ phio,
+__global__ void k_potential(Geo<T> G, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
                             const T *__restrict__ Vn, const T *__restrict__ Vo, const T *__restrict__ Ezn,
                             const T *__restrict__ Ezo, T *__restrict__ A, T *__restrict__ B) {
     PF_ELEM_SMEM(T, G, 3)
+    const Phys<T> q = plane_phys(q_);
     T *sV = sF, *sRx = sF + pp_, *sRy = sF + 2 * pp_;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
@@ -254,13 +268,14 @@ __global__ void k_efield(Geo<T> G, const T *__restrict__ V, T *__restrict__ Ex, 
 // A = -int Q1 w + int grad_2D Q2 . grad_2D w + (alpha + S/eta^2) int_wall U w,
 // U = -Theta'(phi*)/lambda; faceU (optional) = int_wall U w (element-local face slots).
 template <typename T>
-__global__ void k_chem(Geo<T> G, Phys<T> q, const T *__restrict__ phin, const T *__restrict__ phio,
+__global__ void k_chem(Geo<T> G, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
                        const T *__restrict__ dzphin, const T *__restrict__ dzphio,
                        const T *__restrict__ uxn, const T *__restrict__ uxo, const T *__restrict__ uyn,
                        const T *__restrict__ uyo, const T *__restrict__ uzn, const T *__restrict__ uzo,
                        const T *__restrict__ Ex, const T *__restrict__ Ey, const T *__restrict__ Ez,
                        T *__restrict__ A, T *__restrict__ Q2n, T *__restrict__ faceU) {
     PF_ELEM_SMEM(T, G, 4)
+    const Phys<T> q = plane_phys(q_);
     T *sP = sF, *sQ = sF + pp_, *sQx = sF + 2 * pp_, *sQy = sF + 3 * pp_;
     load_tables(G, sD, sDw, sw);
     const ElemIdx e = elem_index(G);
@@ -320,8 +335,9 @@ struct MomOut {
 };
 
 template <typename T>
-__global__ void k_momentum(Geo<T> G, Phys<T> q, MomIn<T> in, MomOut<T> out) {
+__global__ void k_momentum(Geo<T> G, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
     PF_ELEM_SMEM(T, G, 12)
+    const Phys<T> q = plane_phys(q_);
     // inputs with in-plane derivatives: phi, W, u*_x, u*_y, u*_z, P*
     T *sphi = sF, *sW = sF + pp_, *sux = sF + 2 * pp_, *suy = sF + 3 * pp_, *suz = sF + 4 * pp_,
       *sPs = sF + 5 * pp_;
@@ -737,6 +753,112 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
             a.out3[gi] = rw.x + a.S_eta2 * r.x + a.Q2n[gi];
         }
     }
+}
+
+// ---- ensembles of independent 2D runs (blockIdx.y = run): no z transform ---------------------
+// forward: out = scale_p * (DSSUM X0) - (liftb[i] vb_p + liftt[i] vt_p) Mx[j]   (X1, when given,
+// is DSSUM'd nodal Q2 copied to out1 for the phi step)
+template <typename T>
+struct IndepFwd {
+    const T *X0;          // element-local
+    const T *X1;          // nodal (copied to out1) or nullptr
+    const T *scale_p;     // per-run scale or nullptr (then 1)
+    const T *liftb, *liftt, *vb_p, *vt_p;   // lifting (nullable)
+    T *out, *out1;
+};
+
+template <typename T>
+__global__ void k_fwd_indep(Geo<T> G, IndepFwd<T> a) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= G.n2) return;
+    const int p = blockIdx.y;
+    int s[4];
+    dss_sources(G, q, s);
+    const long long lplane = (long long)G.ex * G.ey * G.p * G.p;
+    const long long gi = (long long)p * G.n2 + q;
+    T v = gather4(a.X0, p * lplane, s);
+    if (a.scale_p) v *= a.scale_p[p];
+    if (a.liftb) {
+        const int i = q / G.nx, j = q % G.nx;
+        v -= (a.liftb[i] * a.vb_p[p] + a.liftt[i] * a.vt_p[p]) * G.Mx[j];
+    }
+    a.out[gi] = v;
+    if (a.out1) a.out1[gi] = a.X1[gi];
+}
+
+template <typename T>
+struct IndepInv {
+    const T *Y;               // solution planes
+    int drow0, drow1;         // Dirichlet rows (-1: none) receiving v0_p / v1_p
+    const T *v0_p, *v1_p;
+    T *out;
+    // phi variant
+    const T *psi, *Q2n;
+    T alpha, S_eta2;
+    T *outW, *outL;
+};
+
+template <typename T>
+__global__ void k_inv_indep(Geo<T> G, IndepInv<T> a) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= G.n2) return;
+    const int p = blockIdx.y;
+    const long long gi = (long long)p * G.n2 + q;
+    T x = a.Y[gi];
+    const int i = q / G.nx;
+    if (a.drow0 >= 0 && i == a.drow0) x += a.v0_p[p];
+    if (a.drow1 >= 0 && i == a.drow1) x += a.v1_p[p];
+    a.out[gi] = x;
+    if (a.outW) {
+        const T ps = a.psi[gi];
+        const T W = ps - (a.alpha + a.S_eta2) * x - a.Q2n[gi];
+        a.outW[gi] = W;
+        a.outL[gi] = ps - a.alpha * x;
+    }
+}
+
+// wall face slots of every run summed along x (no z transform)
+template <typename T>
+__global__ void k_face_indep(Geo<T> G, const T *__restrict__ face, T *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G.nx) return;
+    const int p = blockIdx.y, K = G.K, pp = G.p;
+    const long long base = (long long)p * G.ex;
+    T v;
+    if (j % K == 0) v = face[(base + j / K) * pp] + face[(base + (j / K - 1 + G.ex) % G.ex) * pp + K];
+    else v = face[(base + j / K) * pp + j % K];
+    out[(long long)p * G.nx + j] = v;
+}
+
+// per-plane FP64 max |x| (or sum M x with kind 0), one block per plane
+template <typename T>
+__global__ void k_reduce_planes(const T *__restrict__ x, const T *__restrict__ Mx, const T *__restrict__ My,
+                                int nx, int n2, int kind, double *__restrict__ out) {
+    __shared__ double sm[256];
+    const int p = blockIdx.x;
+    const T *xp = x + (long long)p * n2;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        if (kind == 0) {
+            acc += (double)Mx[i % nx] * (double)My[i / nx] * (double)xp[i];
+        } else {
+            const double v = fabs((double)xp[i]);
+            if (acc == acc) {
+                if (v != v) acc = v;
+                else if (v > acc) acc = v;
+            }
+        }
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double a = sm[threadIdx.x], b = sm[threadIdx.x + s];
+            sm[threadIdx.x] = kind == 0 ? a + b : ((a != a || b != b) ? (a != a ? a : b) : fmax(a, b));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[p] = sm[0];
 }
 
 // right-hand side of eq. 57 / 76 in mode space: -M psi_hat (+ wall term rows)

@@ -86,6 +86,16 @@ def load(build_if_missing: bool = True):
     L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
     L.pf_profile.argtypes = [c_void_p, c_int]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
+    L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
+                                  POINTER(POINTER(c_double)), c_void_p, POINTER(c_void_p)]
+    L.pf_batch_step.argtypes = [c_void_p, c_int]
+    L.pf_batch_umax.argtypes = [c_void_p, dp, dp]
+    L.pf_batch_run_to_equilibrium.argtypes = [c_void_p, c_double, c_int, c_int, POINTER(c_int)]
+    L.pf_batch_get_fields.argtypes = [c_void_p, c_int, c_uint, dp, c_size_t]
+    L.pf_batch_autotune.argtypes = [c_void_p, c_int, dp]
+    L.pf_batch_groups.argtypes = [c_void_p, POINTER(c_int)]
+    L.pf_batch_destroy.argtypes = [c_void_p]
+    L.pf_batch_destroy.restype = None
     L.pf_profile_read.argtypes = [c_void_p, dp, POINTER(ctypes.c_longlong)]
     L.pf_destroy.argtypes = [c_void_p]
     L.pf_destroy.restype = None
@@ -277,3 +287,90 @@ def from_workload(wl, precision: int = PF_FP64, stream: Optional[int] = None, dt
     scheme = dict(dt=s.dt if dt is None else dt, bdf=s.bdf, precision=precision, S=s.S, nu_m=s.nu_m,
                   rho0=s.rho0, eps0=s.eps0)
     return Solver(m.xb, m.yb, m.order, m.nz, m.lz, fluid, vbc, scheme, phi0, stream=stream)
+
+
+# ---- ensembles of independent 2D runs --------------------------------------------------------
+class Batch:
+    """Owner of one ``pf_batch``: independent 2D runs advanced together (grouped by mesh)."""
+
+    def __init__(self, workloads_list, precision: int = PF_FP64, stream: Optional[int] = None,
+                 phi0_list=None):
+        import workloads as _wl
+        L = load()
+        n = len(workloads_list)
+        self.n = n
+        self._keep = []
+        meshes = (PfMesh * n)()
+        fluids = (PfFluid * n)()
+        vbcs = (PfVbc * n)()
+        phis = (POINTER(c_double) * n)()
+        self.shapes = []
+        s0 = workloads_list[0].scheme
+        for r, wl in enumerate(workloads_list):
+            m, f, v = wl.mesh, wl.fluid, wl.vbc
+            if m.nz != 1:
+                raise ValueError("ensemble runs must be 2D")
+            xb, yb = _f64(m.xb), _f64(m.yb)
+            x = nodes_1d(xb, m.order, True)
+            y = nodes_1d(yb, m.order, False)
+            phi = _f64(_wl.eval_on_grid(wl.phi0, x, y, None) if phi0_list is None else phi0_list[r]).ravel()
+            self._keep += [xb, yb, phi]
+            meshes[r] = PfMesh(m.ex, m.ey, _dp(xb), _dp(yb), m.order, 1, 1.0)
+            fluids[r] = PfFluid(f.rho1, f.rho2, f.mu1, f.mu2, f.eps1, f.eps2, f.sigma, f.eta, f.gamma1, f.theta_s_deg)
+            vbcs[r] = PfVbc(v.bottom_kind, v.top_kind, v.v_bottom, v.v_top)
+            phis[r] = _dp(phi)
+            self.shapes.append((len(y), len(x)))
+        self.scheme = PfScheme(s0.dt, s0.bdf, int(precision), s0.S, s0.nu_m, s0.rho0, s0.eps0)
+        h = c_void_p()
+        _check(L.pf_batch_create(n, meshes, fluids, vbcs, ctypes.byref(self.scheme), phis, c_void_p(stream or 0),
+                                 ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check_b(load().pf_batch_step(self._h, int(n)))
+
+    def umax(self):
+        u, m = np.zeros(self.n), np.zeros(self.n)
+        _check_b(load().pf_batch_umax(self._h, _dp(u), _dp(m)))
+        return u, m
+
+    def run_to_equilibrium(self, tol: float, max_steps: int, check_every: int = 100):
+        out = (c_int * self.n)()
+        _check_b(load().pf_batch_run_to_equilibrium(self._h, float(tol), int(max_steps), int(check_every), out))
+        return np.array(list(out))
+
+    def get(self, run: int, mask: int) -> dict:
+        ny, nx = self.shapes[run]
+        names = [nm for bit, nms in _BLOCKS if mask & bit for nm in nms]
+        out = np.zeros(len(names) * nx * ny)
+        _check_b(load().pf_batch_get_fields(self._h, int(run), int(mask), _dp(out), out.size))
+        return {nm: out[i * nx * ny:(i + 1) * nx * ny].reshape(1, ny, nx) for i, nm in enumerate(names)}
+
+    def groups(self):
+        g = (c_int * self.n)()
+        ng = load().pf_batch_groups(self._h, g)
+        return ng, np.array(list(g))
+
+    def autotune(self, steps: int = 5):
+        ng, _ = self.groups()
+        ms = np.zeros(max(1, ng))
+        rc = load().pf_batch_autotune(self._h, int(steps), _dp(ms))
+        if rc < 0:
+            _check_b(rc)
+        return ms[:ng]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_b(rc: int):
+    if rc != PF_OK:
+        raise PfError(rc, "ensemble call failed")

@@ -1,0 +1,89 @@
+"""Ensembles of independent 2D runs (pf_batch_*) against the FP64 oracle, run by run."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle.runner import solver_of
+from paper_2305_09020_gb300 import native
+
+from gpu_util import ALL, oracle_fields, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def uneven_runs():
+    """Five runs in three mesh groups, each with its own permittivity ratio and voltage."""
+    runs = []
+    for (ex, ey, K, eps, v) in [(4, 2, 5, 5.0, 1.0), (4, 2, 5, 12.0, 2.5), (4, 2, 5, 2.0, 0.5),
+                                (6, 3, 4, 7.0, 1.5), (2, 2, 6, 3.0, 2.0)]:
+        wl = workloads.small2d(ex=ex, ey=ey, order=K)
+        wl.fluid.eps1 = eps
+        wl.vbc.v_bottom = v
+        runs.append(wl)
+    return runs
+
+
+def _compare(batch, runs, oras, tol, steps):
+    for r, (wl, ora) in enumerate(zip(runs, oras)):
+        got = batch.get(r, ALL)
+        errs = rel_errors(got, oracle_fields(ora), skip=("Ez", "uz") + (("psi",) if steps == 0 else ()))
+        bad = {k: v for k, v in errs.items() if not v <= tol}
+        assert not bad, f"run {r} after {steps} steps: {bad}"
+
+
+def test_batch_fp64_matches_oracle_per_run():
+    runs = uneven_runs()
+    b = native.Batch(runs, precision=native.PF_FP64)
+    assert b.groups()[0] == 3
+    oras = [solver_of(wl) for wl in runs]
+    _compare(b, runs, oras, 1e-11, 0)
+    for _ in range(6):
+        for o in oras:
+            o.step()
+    b.step(6)
+    _compare(b, runs, oras, 1e-11, 6)
+    umax, mass = b.umax()
+    for r, o in enumerate(oras):
+        assert abs(umax[r] - o.umax()) <= 1e-11 * max(o.umax(), 1e-30)
+        assert abs(mass[r] - o.phase_mass()) <= 1e-12 * abs(o.phase_mass())
+    b.close()
+
+
+def test_batch_mixed_and_graph_stream():
+    torch = pytest.importorskip("torch")
+    runs = uneven_runs()
+    s = torch.cuda.Stream()
+    b = native.Batch(runs, precision=native.PF_MIXED, stream=s.cuda_stream)
+    oras = [solver_of(wl) for wl in runs]
+    for _ in range(3):
+        for o in oras:
+            o.step()
+    b.step(3)                     # steps 2 and 3 replay the ensemble graph
+    for r, ora in enumerate(oras):
+        errs = rel_errors(b.get(r, ALL), oracle_fields(ora), skip=("Ez", "uz"))
+        for k, v in errs.items():
+            assert v <= (5e-5 if k in ("V", "phi", "psi") else 5e-4), (r, k, v)
+    b.close()
+
+
+def test_batch_autotune_keeps_lockstep():
+    runs = uneven_runs()
+    b = native.Batch(runs, precision=native.PF_FP64)
+    ms = b.autotune(steps=1)      # one BDF1 step, then 3 x 2 = 6 steps per group
+    assert len(ms) == 3 and np.all(ms > 0)
+    oras = [solver_of(wl) for wl in runs]
+    for _ in range(7):
+        for o in oras:
+            o.step()
+    _compare(b, runs, oras, 1e-11, 7)
+    b.close()
+
+
+def test_batch_run_to_equilibrium_reports_steps():
+    runs = uneven_runs()
+    b = native.Batch(runs, precision=native.PF_FP64)
+    steps = b.run_to_equilibrium(tol=1e30, max_steps=10, check_every=4)
+    assert np.all(steps == 4)
+    steps = b.run_to_equilibrium(tol=0.0, max_steps=10, check_every=4)   # never below 0
+    assert np.all(steps == -1)
+    b.close()
