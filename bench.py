@@ -131,6 +131,40 @@ def fdm_flops_per_step(nx, ny, nz, d3):
     return 4.0 * n2 * (nx + ny) * planes
 
 
+def warmstart_arm(args):
+    """Learned warm start: steps and wall time to equilibrium, warm vs cold (opt-in; minutes)."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2305_09020_gb300 import native, warmstart
+    stream = torch.cuda.Stream()
+    tol, cap, every = args.ws_tol, args.ws_cap, 200
+    train = workloads.warmstart2d(args.ws_train, seed=1)
+    test = workloads.warmstart2d(args.ws_test, seed=10001)
+    t0 = time.perf_counter()
+    f_tr, y_tr, st_tr = warmstart.generate(train, tol, cap, every, stream=stream.cuda_stream)
+    t_gen = time.perf_counter() - t0
+    no = warmstart.make_operator(f_tr, train[0].mesh, seed=0, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    losses = no.train(f_tr, y_tr, batch=64, epochs=args.ws_epochs, lr=1e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    res = warmstart.evaluate(no, test, tol, cap, every, stream=stream.cuda_stream)
+    no.close()
+    line = {"metric": "time-to-equilibrium warm vs cold", "unit": "s", "higher_is_better": False,
+            "value": res["warm"]["run_s"], "cold_value": res["cold"]["run_s"],
+            "criterion": f"max|u| < {tol:g} checked every {every} steps, cap {cap} steps",
+            "config": {"workload": "warm-start ensemble: 16x8 elements order 8, V~U(0,3), eps ratio logU(2,20), "
+                                   "drop radius U(0.15,0.35) on the wall, eta 0.02, dt 1e-4, mixed precision",
+                       "train_runs": len(train), "test_runs": len(test), "seeds": "train 1, test 10001",
+                       "network": "3-128-384-8192 tanh MLP, 128x64 grid, bilinear to GLL nodes, BF16 weights"},
+            "cold": res["cold"], "warm": res["warm"], "final_phi_rel_diff": res["final_phi_rel_diff_warm_vs_cold"],
+            "train": {"generation_s": t_gen, "training_s": t_train, "epochs": args.ws_epochs,
+                      "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                      "train_runs_reaching_tol": int((st_tr >= 0).sum())}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -139,9 +173,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
+    ap.add_argument("--warmstart", action="store_true", help="learned warm start study instead (minutes)")
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-test", type=int, default=200)
+    ap.add_argument("--ws-tol", type=float, default=1e-2)
+    ap.add_argument("--ws-cap", type=int, default=20000)
+    ap.add_argument("--ws-epochs", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.warmstart:
+        return warmstart_arm(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
 

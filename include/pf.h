@@ -233,7 +233,8 @@ int pf_batch_umax(pf_batch *b, double *umax, double *mass);
 
 /* Step until every run has max|u| < tol, checking every check_every steps, or until the
  * ensemble has taken max_steps steps.  steps_out[r] = the step count at which run r was first
- * seen below tol, or -1.  Returns PF_EDIVERGED if a run produced a non-finite value. */
+ * seen below tol, -1 if it never was, or -2 if its velocity became non-finite (runs are
+ * independent: a diverged run does not affect the others, which keep stepping). */
 int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_steps, int check_every, int *steps_out);
 
 /* Copy run r's fields to the host; mask and layout as pf_get_fields for one 2D run. */
@@ -250,6 +251,37 @@ int pf_batch_autotune(pf_batch *b, int steps, double *ms_out);
 int pf_batch_groups(const pf_batch *b, int *group_of);
 
 void pf_batch_destroy(pf_batch *b);
+
+/* ---- learned warm start --------------------------------------------------------------- */
+
+/* A small neural operator (the paper has no counterpart): a tanh multilayer perceptron with
+ * layer widths dims[0..nlayer-1] maps dims[0] run parameters (standardised with feat_mean /
+ * feat_std) to the phase field on a gnx x gny grid (dims[nlayer-1] = gnx*gny; x periodic
+ * on [x0, x1) with cells starting at x0 + i (x1-x0)/gnx, y from y0 to y1 inclusive), which a
+ * fixed bilinear map carries to the nqx x nqy nodes (node_x[nqx], node_y[nqy]; [y][x] order).
+ * Weights are BF16 in the products (FP32 master copies), activations and sums FP32; Glorot
+ * initialisation from seed.  All work runs on cuda_stream.  Errors: PF_EINVAL, PF_ENOMEM,
+ * PF_ECUDA (messages in pf_last_error(NULL)). */
+typedef struct pf_no pf_no;
+int pf_no_create(int nlayer, const int *dims, const double *feat_mean, const double *feat_std, int gnx, int gny,
+                 double x0, double x1, double y0, double y1, int nqx, int nqy, const double *node_x,
+                 const double *node_y, uint64_t seed, void *cuda_stream, pf_no **out);
+/* Number of parameters: for each layer its weights (dims[l] x dims[l+1], row-major) then
+ * its biases, layer after layer. */
+long long pf_no_param_count(const pf_no *h);
+/* FP32 master parameters to / from host doubles (n >= pf_no_param_count). */
+int pf_no_get_params(pf_no *h, double *host, size_t n);
+int pf_no_set_params(pf_no *h, const double *host, size_t n);
+/* Phase field at the nodes (B x nq, host) for B feature rows (B x dims[0], host). */
+int pf_no_predict(pf_no *h, int B, const double *feat, double *phi_nodes);
+/* Mean squared error against target node fields (B x nq) and the gradient of every
+ * parameter (grad nullable; layout of pf_no_get_params). */
+int pf_no_loss_grad(pf_no *h, int B, const double *feat, const double *target, double *loss, double *grad);
+/* Adam training (beta 0.9 / 0.999, eps 1e-8) on nsample rows resident on the device for
+ * `epochs` epochs of shuffled minibatches of `batch` rows; loss_per_epoch[epochs] nullable. */
+int pf_no_train(pf_no *h, int nsample, const double *feat, const double *target, int batch, int epochs,
+                double lr, uint64_t seed, double *loss_per_epoch);
+void pf_no_destroy(pf_no *h);
 
 /* ---- allocation-free solve ---------------------------------------------------------- */
 

@@ -1425,8 +1425,11 @@ extern "C" int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_step
         rc = pf_batch_umax(b, um.data(), nullptr);
         if (rc != PF_OK) return rc;
         for (int r = 0; r < nrun; ++r) {
-            if (!(um[r] == um[r])) return batch_fail(b, PF_EDIVERGED, "non-finite velocity in run " + std::to_string(r));
-            if (steps_out[r] < 0 && um[r] < tol) {
+            if (steps_out[r] != -1) continue;
+            if (!(um[r] == um[r]) || std::isinf(um[r])) {   // runs are independent: record and go on
+                steps_out[r] = -2;
+                --left;
+            } else if (um[r] < tol) {
                 steps_out[r] = (int)b->nstep;
                 --left;
             }

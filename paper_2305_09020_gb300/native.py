@@ -96,6 +96,17 @@ def load(build_if_missing: bool = True):
     L.pf_batch_groups.argtypes = [c_void_p, POINTER(c_int)]
     L.pf_batch_destroy.argtypes = [c_void_p]
     L.pf_batch_destroy.restype = None
+    L.pf_no_create.argtypes = [c_int, POINTER(c_int), dp, dp, c_int, c_int, c_double, c_double, c_double, c_double,
+                               c_int, c_int, dp, dp, ctypes.c_uint64, c_void_p, POINTER(c_void_p)]
+    L.pf_no_param_count.argtypes = [c_void_p]
+    L.pf_no_param_count.restype = ctypes.c_longlong
+    L.pf_no_get_params.argtypes = [c_void_p, dp, c_size_t]
+    L.pf_no_set_params.argtypes = [c_void_p, dp, c_size_t]
+    L.pf_no_predict.argtypes = [c_void_p, c_int, dp, dp]
+    L.pf_no_loss_grad.argtypes = [c_void_p, c_int, dp, dp, dp, dp]
+    L.pf_no_train.argtypes = [c_void_p, c_int, dp, dp, c_int, c_int, c_double, ctypes.c_uint64, dp]
+    L.pf_no_destroy.argtypes = [c_void_p]
+    L.pf_no_destroy.restype = None
     L.pf_profile_read.argtypes = [c_void_p, dp, POINTER(ctypes.c_longlong)]
     L.pf_destroy.argtypes = [c_void_p]
     L.pf_destroy.restype = None
@@ -374,3 +385,65 @@ class Batch:
 def _check_b(rc: int):
     if rc != PF_OK:
         raise PfError(rc, "ensemble call failed")
+
+
+# ---- neural operator (learned warm start) -------------------------------------------------------
+class NeuralOperator:
+    """tanh MLP: run parameters -> phase field on a uniform grid -> bilinear map to GLL nodes."""
+
+    def __init__(self, dims, feat_mean, feat_std, grid, box, node_x, node_y, seed: int = 0,
+                 stream: Optional[int] = None):
+        L = load()
+        self.dims = [int(d) for d in dims]
+        d = (c_int * len(self.dims))(*self.dims)
+        fm, fs = _f64(feat_mean), _f64(feat_std)
+        nxv, nyv = _f64(node_x), _f64(node_y)
+        self.nq = len(nxv) * len(nyv)
+        h = c_void_p()
+        _check(L.pf_no_create(len(self.dims), d, _dp(fm), _dp(fs), int(grid[0]), int(grid[1]), float(box[0]),
+                              float(box[1]), float(box[2]), float(box[3]), len(nxv), len(nyv), _dp(nxv), _dp(nyv),
+                              ctypes.c_uint64(seed), c_void_p(stream or 0), ctypes.byref(h)), None)
+        self._h = h
+        self.nparam = int(L.pf_no_param_count(h))
+
+    def params(self):
+        out = np.zeros(self.nparam)
+        _check(load().pf_no_get_params(self._h, _dp(out), out.size), None)
+        return out
+
+    def set_params(self, p):
+        p = _f64(p)
+        _check(load().pf_no_set_params(self._h, _dp(p), p.size), None)
+
+    def predict(self, feat):
+        feat = _f64(feat).reshape(-1, self.dims[0])
+        out = np.zeros((feat.shape[0], self.nq))
+        _check(load().pf_no_predict(self._h, feat.shape[0], _dp(feat), _dp(out)), None)
+        return out
+
+    def loss_grad(self, feat, target):
+        feat = _f64(feat).reshape(-1, self.dims[0])
+        target = _f64(target).reshape(feat.shape[0], self.nq)
+        loss = np.zeros(1)
+        grad = np.zeros(self.nparam)
+        _check(load().pf_no_loss_grad(self._h, feat.shape[0], _dp(feat), _dp(target), _dp(loss), _dp(grad)), None)
+        return float(loss[0]), grad
+
+    def train(self, feat, target, batch: int = 64, epochs: int = 100, lr: float = 1e-3, seed: int = 0):
+        feat = _f64(feat).reshape(-1, self.dims[0])
+        target = _f64(target).reshape(feat.shape[0], self.nq)
+        losses = np.zeros(max(1, epochs))
+        _check(load().pf_no_train(self._h, feat.shape[0], _dp(feat), _dp(target), int(batch), int(epochs), float(lr),
+                                  ctypes.c_uint64(seed), _dp(losses)), None)
+        return losses[:epochs]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pf_no_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

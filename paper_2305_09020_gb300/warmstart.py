@@ -1,0 +1,83 @@
+"""Learned warm start for equilibrium runs: data generation, training and evaluation.
+
+Orchestration only: every time step runs in the ensemble engine (pf_batch_*), every network
+forward/backward/update in the library's kernels (pf_no_*); this module moves arrays.
+
+* ``generate``   runs batches of independent 2D runs on one fixed mesh until every run has
+  max|u| < tol or the step cap, and returns the run features (V, permittivity ratio, drop
+  area), the phase field at the end (the equilibrium target) and the steps each run needed.
+* ``make_operator`` / ``train``  the network of ``native.NeuralOperator``: 3 -> 128 -> 384 ->
+  128x64 grid (tanh), bilinear to the GLL nodes, BF16 weights.
+* ``evaluate``  runs held-out cases twice, from the usual initial profile (cold) and from the
+  network's prediction (warm), and reports steps and wall time to the criterion and the
+  difference between the two final states.
+"""
+from __future__ import annotations
+
+import time
+from typing import List, Optional
+
+import numpy as np
+
+import workloads
+from . import native
+
+GRID = (128, 64)
+BOX = (0.0, 2.0, 0.0, 1.0)
+DIMS = [3, 128, 384, GRID[0] * GRID[1]]
+
+
+def _chunks(seq, n):
+    for i in range(0, len(seq), n):
+        yield seq[i:i + n]
+
+
+def generate(runs: List[workloads.Workload], tol: float, max_steps: int, check_every: int = 200,
+             precision: int = native.PF_MIXED, stream: Optional[int] = None, batch: int = 256):
+    feats, finals, steps = [], [], []
+    for chunk in _chunks(runs, batch):
+        b = native.Batch(chunk, precision=precision, stream=stream)
+        st = b.run_to_equilibrium(tol, max_steps, check_every)
+        for r in range(len(chunk)):
+            finals.append(b.get(r, native.PF_FIELD_PHI)["phi"].ravel())
+        b.close()
+        feats.extend(workloads.warmstart_features(w) for w in chunk)
+        steps.extend(st.tolist())
+    feats, finals, steps = np.array(feats), np.array(finals), np.array(steps)
+    ok = (steps != -2) & np.all(np.isfinite(finals), axis=1)     # drop runs that diverged
+    return feats[ok], finals[ok], steps[ok]
+
+
+def make_operator(feats: np.ndarray, mesh: workloads.Mesh, seed: int = 0, stream: Optional[int] = None):
+    node_x = native.nodes_1d(mesh.xb, mesh.order, True)
+    node_y = native.nodes_1d(mesh.yb, mesh.order, False)
+    return native.NeuralOperator(DIMS, feats.mean(axis=0), feats.std(axis=0) + 1e-12, GRID, BOX, node_x, node_y,
+                                 seed=seed, stream=stream)
+
+
+def evaluate(no, runs: List[workloads.Workload], tol: float, max_steps: int, check_every: int = 200,
+             precision: int = native.PF_MIXED, stream: Optional[int] = None):
+    feats = np.array([workloads.warmstart_features(w) for w in runs])
+    pred = no.predict(feats)
+    out = {}
+    finals, steps = {}, {}
+    for mode in ("cold", "warm"):
+        t0 = time.perf_counter()
+        b = native.Batch(runs, precision=precision, stream=stream,
+                         phi0_list=None if mode == "cold" else list(pred))
+        t1 = time.perf_counter()
+        st = b.run_to_equilibrium(tol, max_steps, check_every)
+        t2 = time.perf_counter()
+        finals[mode] = np.array([b.get(r, native.PF_FIELD_PHI)["phi"].ravel() for r in range(len(runs))])
+        b.close()
+        steps[mode] = st
+        out[mode] = {"setup_s": t1 - t0, "run_s": t2 - t1, "diverged": int((st == -2).sum()),
+                     "capped": int((st == -1).sum())}
+    # compare the runs that neither side lost to divergence; capped runs count as the cap
+    ok = (steps["cold"] != -2) & (steps["warm"] != -2)
+    for mode in ("cold", "warm"):
+        s = np.where(steps[mode] == -1, max_steps, steps[mode])[ok]
+        out[mode].update({"steps_mean": float(s.mean()), "steps_median": float(np.median(s)), "runs": int(ok.sum())})
+    diff = np.linalg.norm(finals["warm"][ok] - finals["cold"][ok], axis=1) / np.linalg.norm(finals["cold"][ok], axis=1)
+    out["final_phi_rel_diff_warm_vs_cold"] = {"median": float(np.median(diff)), "max": float(diff.max())}
+    return out

@@ -273,3 +273,41 @@ def eval_on_grid(fn: Callable, x: np.ndarray, y: np.ndarray, z: Optional[np.ndar
     Z, Y, X = np.meshgrid(zz, np.asarray(y, dtype=np.float64), np.asarray(x, dtype=np.float64),
                           indexing="ij")
     return np.ascontiguousarray(fn(X, Y, Z), dtype=np.float64)
+
+
+def warmstart2d(n: int, seed: int) -> List[Workload]:
+    """Runs for the learned warm start: one fixed mesh (16x8 elements, order 8) so that only the
+    voltage V ~ U(0,3), the permittivity ratio ~ logU(2,20) and the drop radius ~ U(0.15,0.35)
+    (drop centred on the wall, hence its volume) vary; eta = 0.02, dt = 1e-4."""
+    rng = np.random.default_rng(seed)
+    eta = 0.02
+    out = []
+    for i in range(n):
+        v = float(rng.uniform(0.0, 3.0))
+        eps_ratio = float(math.exp(rng.uniform(math.log(2.0), math.log(20.0))))
+        radius = float(rng.uniform(0.15, 0.35))
+
+        def phi0(x, y, z, r0=radius):
+            r = np.sqrt((x - 1.0) ** 2 + y ** 2)
+            return _tanh_profile(r0 - r, eta)
+
+        out.append(Workload(
+            name=f"warmstart2d_{seed}_{i}",
+            mesh=Mesh(xb=np.linspace(0.0, 2.0, 17), yb=np.linspace(0.0, 1.0, 9), order=8),
+            fluid=Fluid(rho1=1.0, rho2=1.0, mu1=1.0, mu2=1.0, eps1=eps_ratio, eps2=1.0,
+                        sigma=1.0, eta=eta, gamma1=1e-4),
+            vbc=VoltageBC(BC_DIRICHLET, BC_DIRICHLET, v_bottom=v, v_top=0.0),
+            scheme=Scheme(dt=1e-4),
+            steps=200000,
+            phi0=phi0,
+            seed=seed,
+        ))
+    return out
+
+
+def warmstart_features(wl: Workload) -> np.ndarray:
+    """(V, permittivity ratio, drop area) of a warm-start run: the network's three inputs."""
+    # the drop is a half disc on the wall: area pi r^2 / 2, recovered from the initial profile's
+    # parameters stored in the closure default
+    r0 = wl.phi0.__defaults__[0]
+    return np.array([wl.vbc.v_bottom, wl.fluid.eps1 / wl.fluid.eps2, 0.5 * math.pi * r0 ** 2])
