@@ -173,6 +173,7 @@ struct Engine {
     std::vector<TcB> tcb;
     bool use_tc = false;
     int simt_tile = 0;   // SIMT GEMM tile: 0 heuristic, 32 or 64 forced (autotuner)
+    int tp_override = 0; // pencils per transform block: 0 heuristic, else forced (autotuner)
     // steady-state (BDF2) step captured once per history-slot parity; replayed by pf_step
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2][PF_KC_COUNT] = {};
@@ -418,7 +419,7 @@ struct Engine {
     // pencils per transform block: enough blocks for 4 per SM, shared memory <= 24 KiB
     int fwd_tp() const {
         int tp = (int)(24576 / (sizeof(cplx<T>) * (nz + 1)));
-        const int by_grid = n2 / (4 * 152);
+        const int by_grid = tp_override > 0 ? tp_override : n2 / (4 * 152);
         if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;
         if (tp < 4) tp = 4;
@@ -1189,6 +1190,80 @@ extern "C" int pf_profile_read(pf_handle *h, double *ms, long long *launches) {
     for (int k = 0; k < PF_KC_COUNT; ++k) {
         if (ms) ms[k] = h->prof.on ? h->prof.ms[k] : 0.0;
         if (launches) launches[k] = h->prof.launches[k];
+    }
+    return PF_OK;
+}
+
+namespace {
+// time `steps` steady steps of each transform variant, keep the fastest; advances `total` steps
+template <typename T>
+void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEvent_t e1, int *choice, double *best_ms) {
+    struct Cand { bool tc; int tile; };
+    std::vector<Cand> cands;
+    if (!E.tcb.empty()) cands.push_back({true, 0});
+    cands.push_back({false, 32});
+    cands.push_back({false, 64});
+    Cand pick = cands[0];
+    double best = INFINITY;
+    int taken = 0;
+    for (const Cand &c : cands) {
+        E.use_tc = c.tc;
+        E.simt_tile = c.tile;
+        E.step(2);
+        PF_CU(cudaEventRecord(e0, E.st));
+        for (int s = 0; s < steps; ++s) E.step(2);
+        PF_CU(cudaEventRecord(e1, E.st));
+        PF_CU(cudaEventSynchronize(e1));
+        taken += steps + 1;
+        float ms = 0.f;
+        PF_CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / steps < best) { best = ms / steps; pick = c; }
+    }
+    E.use_tc = pick.tc;
+    E.simt_tile = pick.tile;
+    // then the transform tile (pencils per block), with the chosen GEMM
+    if (E.d3) {
+        int best_tp = 0;
+        for (int tp : {4, 8, 16, 32}) {
+            E.tp_override = tp;
+            E.step(2);
+            PF_CU(cudaEventRecord(e0, E.st));
+            for (int s = 0; s < steps; ++s) E.step(2);
+            PF_CU(cudaEventRecord(e1, E.st));
+            PF_CU(cudaEventSynchronize(e1));
+            taken += steps + 1;
+            float ms = 0.f;
+            PF_CU(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / steps < best) { best = ms / steps; best_tp = tp; }
+        }
+        E.tp_override = best_tp;
+    }
+    for (; taken < total; ++taken) E.step(2);
+    for (int c = 0; c < 2; ++c)
+        if (E.graph[c]) { cudaGraphExecDestroy(E.graph[c]); E.graph[c] = nullptr; }
+    if (choice) *choice = (pick.tc ? 0 : pick.tile) + 1000 * E.tp_override;
+    if (best_ms) *best_ms = best;
+}
+}  // namespace
+
+extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step) {
+    if (!h || steps < 1) return PF_EINVAL;
+    try {
+        if (h->nstep < 1) pf_step(h, 1);
+        int total = 7 * (steps + 1);
+        if (total % 2) total += 1;
+        cudaEvent_t e0, e1;
+        PF_CU(cudaEventCreate(&e0));
+        PF_CU(cudaEventCreate(&e1));
+        if (h->e64) autotune_engine(*h->e64, steps, total, e0, e1, choice, ms_per_step);
+        else autotune_engine(*h->e32, steps, total, e0, e1, choice, ms_per_step);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->nstep += total;
+        h->t += total * h->hs.dt;
+        h->last_J = 2;
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
     }
     return PF_OK;
 }

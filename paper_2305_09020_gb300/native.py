@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     L.pf_solve_helmholtz.argtypes = [c_void_p, c_int, c_int, c_double, dp, dp]
     L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
     L.pf_profile.argtypes = [c_void_p, c_int]
+    L.pf_autotune.argtypes = [c_void_p, c_int, POINTER(c_int), dp]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
                                   POINTER(POINTER(c_double)), c_void_p, POINTER(c_void_p)]
@@ -254,6 +255,13 @@ class Solver:
         out = np.zeros_like(rhs)
         _check(load().pf_solve_helmholtz(self._h, int(bcset), int(mode), float(lam), _dp(rhs), _dp(out)), self._h)
         return out
+
+    def autotune(self, steps: int = 5):
+        """Pick the fastest transform GEMM and z-transform tile; returns (gemm + 1000 * tile, ms/step)."""
+        ch = c_int()
+        ms = np.zeros(1)
+        _check(load().pf_autotune(self._h, int(steps), ctypes.byref(ch), _dp(ms)), self._h)
+        return int(ch.value), float(ms[0])
 
     def profile(self, enable: bool):
         _check(load().pf_profile(self._h, int(bool(enable))), self._h)

@@ -1,0 +1,70 @@
+"""Checks at the benchmark's full size (droplet3d: 16x8 elements of order 8 x Nz = 64), where the
+oracle would need minutes per step: properties that hold at any size.
+
+* Mirror symmetry: the initial drop is symmetric in x about x = 1 and in z about z = 0.5, the mesh
+  and the boundary conditions too, so phi, V, P, u_x, u_y stay symmetric and u_z antisymmetric
+  under z -> 1 - z (u_x antisymmetric under x -> 2 - x).
+* Phase mass: the first step starts from rest (u* = 0), so int phi is conserved to round-off
+  (the identity from eqs. 56/57 with test function 1).
+* The mixed path stays within its tolerances of the FP64 path."""
+import numpy as np
+import pytest
+
+import workloads
+from paper_2305_09020_gb300 import native
+
+from gpu_util import ALL
+
+pytestmark = pytest.mark.gpu
+
+
+def mirror_x(f):
+    # nodes x_j = x of a uniform periodic GLL grid on [0, 2): x -> 2 - x maps node j to (n - j) mod n
+    n = f.shape[-1]
+    return f[..., (-np.arange(n)) % n]
+
+
+def mirror_z(f):
+    nz = f.shape[0]
+    return f[(nz - np.arange(nz)) % nz]     # z_j = j/nz -> 1 - z_j = z_{nz - j}
+
+
+@pytest.fixture(scope="module")
+def fp64_run():
+    wl = workloads.droplet3d()
+    h = native.from_workload(wl, precision=native.PF_FP64)
+    m0 = h.diagnostics()[0]
+    h.step(1)
+    m1 = h.diagnostics()[0]
+    h.step(4)
+    f = h.get(ALL)
+    h.close()
+    return wl, m0, m1, f
+
+
+def test_fullsize_mass_conserved_from_rest(fp64_run):
+    _, m0, m1, _ = fp64_run
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+
+
+def test_fullsize_mirror_symmetry(fp64_run):
+    _, _, _, f = fp64_run
+    scale = {k: max(np.max(np.abs(v)), 1e-300) for k, v in f.items()}
+    for k in ("V", "phi", "P", "uy", "Ey"):
+        assert np.max(np.abs(f[k] - mirror_z(f[k]))) <= 1e-11 * scale[k], k
+        assert np.max(np.abs(f[k] - mirror_x(f[k]))) <= 1e-11 * scale[k], k
+    assert np.max(np.abs(f["uz"] + mirror_z(f["uz"]))) <= 1e-11 * scale["uz"]
+    assert np.max(np.abs(f["ux"] + mirror_x(f["ux"]))) <= 1e-11 * scale["ux"]
+    assert scale["uz"] > 1e-10 and scale["ux"] > 1e-10          # the drop moves
+
+
+def test_fullsize_mixed_within_bars_of_fp64(fp64_run):
+    wl, _, _, f64 = fp64_run
+    h = native.from_workload(wl, precision=native.PF_MIXED)
+    h.step(5)
+    f32 = h.get(ALL)
+    h.close()
+    for k in ("V", "phi", "psi"):
+        assert np.linalg.norm(f32[k] - f64[k]) <= 5e-5 * np.linalg.norm(f64[k]), k
+    for k in ("Ex", "Ey", "Ez", "P", "ux", "uy", "uz"):
+        assert np.linalg.norm(f32[k] - f64[k]) <= 5e-4 * np.linalg.norm(f64[k]), k
