@@ -107,7 +107,13 @@ typedef struct {
     double nu_m;        /* 0 -> max(mu1,mu2)/min(rho1,rho2)                                */
     double rho0;        /* 0 -> min(rho1,rho2)                                             */
     double eps0;        /* 0 -> max(eps1,eps2)                                             */
+    int model;          /* PF_MODEL_FULL, or PF_MODEL_EQUILIBRIUM: the simpler system of     */
+                        /* Sec. 2.4 (eq. 16 with eq. 15c, 15d, u = 0; only the V and phi     */
+                        /* sub-steps run, P and u stay 0)                                    */
 } pf_scheme;
+
+#define PF_MODEL_FULL        0
+#define PF_MODEL_EQUILIBRIUM 1
 
 /* ---- host-only set-up helpers (no GPU needed) ------------------------------------------ */
 
@@ -170,7 +176,8 @@ int pf_set_fields(pf_handle *h, unsigned mask, const double *host_in, size_t n, 
 
 /* FP64 diagnostics (synchronous): out[0] = int phi (phase mass), out[1] = max|u|,
  * out[2] = time t, out[3] = step count, out[4] = number of V^0 fixed-point
- * iterations, out[5] = 1 if a non-finite value was seen, out[6..7] = 0. */
+ * iterations, out[5] = 1 if a non-finite value was seen, out[6] = max|phi^n - phi^{n-1}| / dt
+ * (the pseudo-time rate of the equilibrium model), out[7] = 0. */
 int pf_diagnostics(pf_handle *h, double out[8]);
 
 /* One fast-diagonalisation solve on a user right-hand side (synchronous):
@@ -236,7 +243,9 @@ int pf_batch_create(int nrun, const pf_mesh *meshes, const pf_fluid *fluids, con
 /* Advance every run nsteps time steps (Algorithm 1; BDF1 for the first step). */
 int pf_batch_step(pf_batch *b, int nsteps);
 
-/* Per-run FP64 max |u| (out[nrun]) and phase mass int phi (mass[nrun], nullable); synchronous. */
+/* Per-run FP64 max |u| (out[nrun]) and phase mass int phi (mass[nrun], nullable); synchronous.
+ * For PF_MODEL_EQUILIBRIUM (u = 0) umax[r] is the pseudo-time rate max|phi^n - phi^{n-1}| / dt,
+ * so pf_batch_run_to_equilibrium stops on it. */
 int pf_batch_umax(pf_batch *b, double *umax, double *mass);
 
 /* Step until every run has max|u| < tol, checking every check_every steps, or until the

@@ -12,7 +12,8 @@ def params_of(wl, dt=None, bdf=None) -> Params:
     return Params(rho1=f.rho1, rho2=f.rho2, mu1=f.mu1, mu2=f.mu2, eps1=f.eps1, eps2=f.eps2,
                   sigma=f.sigma, eta=f.eta, gamma1=f.gamma1, theta_s_deg=f.theta_s_deg,
                   dt=s.dt if dt is None else dt, bdf=s.bdf if bdf is None else bdf,
-                  S=s.S, nu_m=s.nu_m, rho0=s.rho0, eps0=s.eps0)
+                  S=s.S, nu_m=s.nu_m, rho0=s.rho0, eps0=s.eps0,
+                  equilibrium=bool(getattr(s, "equilibrium", False)))
 
 
 def solver_of(wl, init=True, **kw) -> Solver:

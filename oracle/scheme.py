@@ -38,6 +38,9 @@ Readings of the paper taken here (each also listed in the design notes):
   gamma1 dt)) with gamma0 of the run's BDF order; a discriminant below 1e-10
   in the formula for alpha is set to 0.
 
+With ``Params(equilibrium=True)`` the step is that of the simpler equilibrium system of Sec. 2.4
+(eq. 16 with eq. 15c, 15d): the V and phi sub-steps with u = 0; P and u are not computed.
+
 Parity status: pinned by tests/test_oracle_scheme.py (manufactured solutions
 of eq. 80/81 converge spectrally in K and at second order in dt; reduction
 consistency for phi = 1; series-capacitor potential of flat layers; discrete
@@ -77,6 +80,7 @@ class Params:
     nu_m: float = 0.0
     rho0: float = 0.0
     eps0: float = 0.0
+    equilibrium: bool = False   # Sec. 2.4 simpler system: eq. (16) + eq. (15c, d), u = 0
 
     def __post_init__(self):
         # Sec. 2.1: lambda = 3 sigma eta / (2 sqrt 2)
@@ -413,6 +417,17 @@ class Solver:
             phih[k] = self.solve("phi", -al + self.beta[k] ** 2, ("phi", J, k), r)
         phi1 = self.ifft(phih)
         psi1 = self.ifft(psih)
+
+        if p.equilibrium:
+            # Sec. 2.4: the equilibrium solution has u = 0; eq. (16) is marched in pseudo-time with
+            # the same V and phi steps (u* = 0 in Q1), and neither P nor u is computed
+            self.V_old, self.V = self.V, V1
+            self.phi_old, self.phi = self.phi, phi1
+            self.E = E
+            self.psi = psi1
+            self.t = t1
+            self.nstep += 1
+            return
 
         # ---- P^{n+1}: eq. (58) / (77), T from eq. (49)
         phiL = self.loc(phi1)

@@ -5,9 +5,10 @@
 // levels of the state, element-local right-hand sides and mode-plane work arrays.
 // A step is the kernel sequence of Algorithm 1 / Algorithm 2:
 //   k_potential -> k_fwd -> FDM -> k_inv (V, Ez) -> k_efield (Ex, Ey)
-//   k_chem -> k_fwd (psi RHS, Q2 modes) -> FDM (psi) -> k_rhs_phi -> FDM (phi)
-//   k_inv (phi, dphi/dz, W, dW/dz, L) -> k_momentum -> k_fwd -> FDM (P) -> k_inv (P)
-//   k_ugradp -> k_fwd x d -> FDM (u, all components batched) -> k_inv x d
+//   k_chem -> k_fwd (psi RHS, Q2 modes) -> FDM (psi; its last transform also writes the phi
+//   right-hand side -M psi) -> FDM (phi) -> k_inv (phi, dphi/dz, W, dW/dz, L)
+//   k_momentum -> k_fwd -> FDM (P) -> k_inv (P)
+//   k_ugradp -> k_fwd (all components) -> FDM (u, batched) -> k_inv (all components)
 // The new level is written over level n-1, then the two levels swap roles.
 #include <cuda_runtime.h>
 
@@ -54,6 +55,7 @@ struct HostSetup {
     double rho1, rho2, mu1, mu2, eps1, eps2, sigma, eta, gamma1, theta;
     double dt, S, nu_m, rho0, eps0, lam, cos_theta;
     int bdf, precision;
+    int model = PF_MODEL_FULL;
     // ensemble of independent 2D runs (batch > 0): per-run permittivities and voltages
     int batch = 0;
     std::vector<double> beps1, beps2, bvb, bvt;
@@ -295,11 +297,14 @@ struct Engine {
         shTmp = mk<T>(3 * nz);
         for (int l = 0; l < 2; ++l) {
             V[l] = mk<T>(N); phi[l] = mk<T>(N); P[l] = mk<T>(N);
-            for (int c = 0; c < 3; ++c) u[l == 0 ? c : c][l] = nullptr;
-            for (int c = 0; c < (d3 ? 3 : 2); ++c) u[c][l] = mk<T>(N);
+            for (int c = 0; c < 3; ++c) u[c][l] = nullptr;
+            const int dcomp = d3 ? 3 : 2;
+            T *ub = mk<T>((size_t)dcomp * N);   // components contiguous: batched transforms
+            for (int c = 0; c < dcomp; ++c) u[c][l] = ub + (size_t)c * N;
             if (d3) {
                 Ez[l] = mk<T>(N); dzphi[l] = mk<T>(N); dzP[l] = mk<T>(N);
-                for (int c = 0; c < 3; ++c) dzu[c][l] = mk<T>(N);
+                T *db = mk<T>((size_t)3 * N);
+                for (int c = 0; c < 3; ++c) dzu[c][l] = db + (size_t)c * N;
             } else {
                 Ez[l] = dzphi[l] = dzP[l] = nullptr;
                 for (int c = 0; c < 3; ++c) dzu[c][l] = nullptr;
@@ -310,9 +315,14 @@ struct Engine {
         dzW = d3 ? mk<T>(N) : nullptr;
         LA = mk<T>(NL);
         LB = d3 ? mk<T>(NL) : nullptr;
-        for (int c = 0; c < 3; ++c) {
-            LAU[c] = (c < 2 || d3) ? mk<T>(NL) : nullptr;
-            LBU[c] = d3 ? mk<T>(NL) : nullptr;
+        {
+            const int dcomp = d3 ? 3 : 2;
+            T *la = mk<T>((size_t)dcomp * NL);
+            T *lb = d3 ? mk<T>((size_t)3 * NL) : nullptr;
+            for (int c = 0; c < 3; ++c) {
+                LAU[c] = c < dcomp ? la + (size_t)c * NL : nullptr;
+                LBU[c] = d3 ? lb + (size_t)c * NL : nullptr;
+            }
         }
         faceU = mk<T>((size_t)ex * p * nz);
         RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
@@ -428,7 +438,7 @@ struct Engine {
     void check_launch() { PF_CU(cudaGetLastError()); }
 
     void gemm(const T *A, const T *B, T *C, long long Mrows, int Ncol, int R, int store, const T *lamN,
-              const T *lamR, const T *cpl, int cpl_mod) {
+              const T *lamR, const T *cpl, int cpl_mod, T *C2 = nullptr, const T *face2 = nullptr) {
         if (use_tc) {
             for (auto &t : tcb) {
                 if (t.key != B) continue;
@@ -443,6 +453,10 @@ struct Engine {
                 a.lamR = reinterpret_cast<const float *>(lamR);
                 a.cpl = reinterpret_cast<const float *>(cpl);
                 a.cpl_mod = cpl_mod; a.err = dev_err;
+                a.C2 = reinterpret_cast<float *>(C2);
+                a.m2x = reinterpret_cast<const float *>(Mx);
+                a.m2y = reinterpret_cast<const float *>(My);
+                a.face2 = reinterpret_cast<const float *>(face2);
                 const unsigned mt = (unsigned)((Mrows + 127) / 128);
                 prof->begin(PF_KC_GEMM, st);
                 pf::k_gemm_tc<16><<<dim3(mt, (Ncol + 15) / 16), 128, tc_smem(16), st>>>(a);
@@ -451,7 +465,7 @@ struct Engine {
                 return;
             }
         }
-        pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod};
+        pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod, C2, Mx, My, face2};
         constexpr int BK = sizeof(T) == 8 ? 8 : 16;
         const long long tiles64 = ((Ncol + 63) / 64) * ((Mrows + 63) / 64);
         prof->begin(PF_KC_GEMM, st);
@@ -469,35 +483,38 @@ struct Engine {
     }
 
     // fast-diagonalisation solve of nplanes mode planes: out = S_y [ (S_y^T rhs S_x) / (L_y + L_x + c_p) ] S_x^T
-    void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes) {
+    void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
+             const T *face = nullptr) {
         const long long P = nplanes;
         gemm(rhs, Sx, W1, P * ny, nx, ny, 1, nullptr, nullptr, nullptr, 1);
         gemm(W1, Sy[bcset], W2, P * nx, ny, nx, 0, Ly[bcset], Lx, sh, nz);
         gemm(W2, SyT[bcset], W1, P * nx, ny, nx, 1, nullptr, nullptr, nullptr, 1);
-        gemm(W1, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1);
+        gemm(W1, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1, minus_m_out, face);
     }
 
     void fwd(const T *X0, int x0l, const T *X1, int x1l, int mult, double scale, const T *lift, T *out,
-             T *out1) {
+             T *out1, int ncomp = 1) {
         pf::FwdArgs<T> a;
+        a.cs_x0 = x0l ? NL : N; a.cs_x1 = x1l ? NL : N; a.cs_out = N;
         a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int);
         prof->begin(PF_KC_FWD, st);
-        pf::k_fwd<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        pf::k_fwd<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
         check_launch();
         prof->end(st);
     }
 
-    void inv(const T *Y, T *out, T *dzout, int drow0, double v0, int drow1, double v1) {
+    void inv(const T *Y, T *out, T *dzout, int drow0, double v0, int drow1, double v1, int ncomp = 1) {
         pf::InvArgs<T> a{};
+        a.cs_y = N; a.cs_out = N;
         a.Y = Y; a.phi_variant = 0; a.drow0 = drow0; a.drow1 = drow1; a.v0 = (T)v0; a.v1 = (T)v1;
         a.out = out; a.dzout = d3 ? dzout : nullptr; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
         prof->begin(PF_KC_INV, st);
-        pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        pf::k_inv<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
         check_launch();
         prof->end(st);
     }
@@ -516,15 +533,16 @@ struct Engine {
         prof->end(st);
     }
 
-    void fwd_indep(const T *X0, const T *X1, const T *scale_p, bool lift, T *out, T *out1) {
-        pf::IndepFwd<T> a{X0, X1, scale_p, lift ? liftb : nullptr, lift ? liftt : nullptr, pvb, pvt, out, out1};
+    void fwd_indep(const T *X0, const T *X1, const T *scale_p, bool lift, T *out, T *out1, int ncomp = 1) {
+        pf::IndepFwd<T> a{NL, N, X0, X1, scale_p, lift ? liftb : nullptr, lift ? liftt : nullptr, pvb, pvt, out, out1};
         prof->begin(PF_KC_FWD, st);
-        pf::k_fwd_indep<T><<<dim3((n2 + 255) / 256, nz), 256, 0, st>>>(geo(), a);
+        pf::k_fwd_indep<T><<<dim3((n2 + 255) / 256, nz, ncomp), 256, 0, st>>>(geo(), a);
         check_launch();
         prof->end(st);
     }
-    void inv_indep(const T *Y, T *out, bool dirichlet_v, bool phi_variant, double alpha) {
+    void inv_indep(const T *Y, T *out, bool dirichlet_v, bool phi_variant, double alpha, int ncomp = 1) {
         pf::IndepInv<T> a{};
+        a.cs_y = N; a.cs_out = N;
         a.Y = Y; a.out = out;
         a.drow0 = dirichlet_v ? hs.vrow0 : -1; a.drow1 = dirichlet_v ? hs.vrow1 : -1;
         a.v0_p = pvb; a.v1_p = pvt;
@@ -533,7 +551,7 @@ struct Engine {
             a.outW = W; a.outL = Lf;
         }
         prof->begin(PF_KC_INV, st);
-        pf::k_inv_indep<T><<<dim3((n2 + 255) / 256, nz), 256, 0, st>>>(geo(), a);
+        pf::k_inv_indep<T><<<dim3((n2 + 255) / 256, nz, ncomp), 256, 0, st>>>(geo(), a);
         check_launch();
         prof->end(st);
     }
@@ -581,8 +599,7 @@ struct Engine {
         prof->end(st);
         if (indep) fwd_indep(LA, Q2, nullptr, false, RHS, Q2H);
         else fwd(LA, 1, Q2, 0, 1, 1.0, nullptr, RHS, Q2H);
-        fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz);
-        // phi^{n+1}
+        // wall term of the phi equation (only with a contact angle other than 90 degrees)
         const T *faceh = nullptr;
         if (q.wetting && indep) {
             prof->begin(PF_KC_OTHER, st);
@@ -599,13 +616,17 @@ struct Engine {
             prof->end(st);
             faceh = FACEH;
         }
-        prof->begin(PF_KC_OTHER, st);
-        pf::k_rhs_phi<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(G, PSIH, faceh, RHS);
-        check_launch();
-        prof->end(st);
-        fdm(RHS, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
+        // psi^{n+1}; its last transform also writes the phi right-hand side -M psi (+ wall term)
+        T *rhs_phi = RHS + N;
+        fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz, rhs_phi, faceh);
+        // phi^{n+1}
+        fdm(rhs_phi, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
         if (indep) inv_indep(OUT, phi[o], false, true, al);
         else inv_phi(al, phi[o], dzphi[o]);
+        if (hs.model == PF_MODEL_EQUILIBRIUM) {   // Sec. 2.4: u = 0, no pressure or velocity step
+            cur = o;
+            return;
+        }
         // P^{n+1}
         pf::MomIn<T> mi;
         mi.phi = phi[o]; mi.dzphi = dzphi[o]; mi.W = W; mi.dzW = dzW; mi.L = Lf;
@@ -633,21 +654,18 @@ struct Engine {
         check_launch();
         prof->end(st);
         const int dc = d3 ? 3 : 2;
-        for (int c = 0; c < dc; ++c) {
-            if (indep) fwd_indep(LAU[c], nullptr, nullptr, false, RHS + c * N, nullptr);
-            else fwd(LAU[c], 1, d3 ? LBU[c] : nullptr, 1, 0, 1.0, nullptr, RHS + c * N, nullptr);
-        }
+        // all velocity components in one launch per transform
+        if (indep) fwd_indep(LAU[0], nullptr, nullptr, false, RHS, nullptr, dc);
+        else fwd(LAU[0], 1, d3 ? LBU[0] : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr, dc);
         fdm(RHS, OUT, PF_BCSET_U, shU[J - 1], dc * nz);
-        for (int c = 0; c < dc; ++c) {
-            if (indep) inv_indep(OUT + c * N, u[c][o], false, false, 0.0);
-            else inv(OUT + c * N, u[c][o], dzu[c][o], -1, 0.0, -1, 0.0);
-        }
+        if (indep) inv_indep(OUT, u[0][o], false, false, 0.0, dc);
+        else inv(OUT, u[0][o], dzu[0][o], -1, 0.0, -1, 0.0, dc);
         cur = o;
     }
 
     // per-plane FP64 reduction (kind 0: sum of M x, kind 1: max |x|) of level-n field x into host out[nz]
-    void reduce_planes(const T *x, int kind, double *out) {
-        pf::k_reduce_planes<T><<<nz, 256, 0, st>>>(x, Mx, My, nx, n2, kind, red);
+    void reduce_planes(const T *x, int kind, double *out, const T *y = nullptr) {
+        pf::k_reduce_planes<T><<<nz, 256, 0, st>>>(x, y, Mx, My, nx, n2, kind, red);
         check_launch();
         PF_CU(cudaMemcpyAsync(out, red, nz * sizeof(double), cudaMemcpyDeviceToHost, st));
         PF_CU(cudaStreamSynchronize(st));
@@ -889,12 +907,13 @@ int fill_setup(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, co
     if (!(scheme->dt > 0) || (scheme->bdf != 1 && scheme->bdf != 2)) return bad("bad dt or bdf");
     if (scheme->precision != PF_FP64 && scheme->precision != PF_MIXED && scheme->precision != PF_MIXED_SIMT)
         return bad("bad precision");
+    if (scheme->model != PF_MODEL_FULL && scheme->model != PF_MODEL_EQUILIBRIUM) return bad("bad model");
     s.ex = mesh->ex; s.ey = mesh->ey; s.K = mesh->order; s.nz = mesh->nz; s.lz = mesh->nz > 1 ? mesh->lz : 1.0;
     s.xb.assign(mesh->xb, mesh->xb + s.ex + 1);
     s.yb.assign(mesh->yb, mesh->yb + s.ey + 1);
     s.rho1 = f.rho1; s.rho2 = f.rho2; s.mu1 = f.mu1; s.mu2 = f.mu2; s.eps1 = f.eps1; s.eps2 = f.eps2;
     s.sigma = f.sigma; s.eta = f.eta; s.gamma1 = f.gamma1; s.theta = f.theta_s_deg;
-    s.dt = scheme->dt; s.bdf = scheme->bdf; s.precision = scheme->precision;
+    s.dt = scheme->dt; s.bdf = scheme->bdf; s.precision = scheme->precision; s.model = scheme->model;
     // Sec. 2.1 and Sec. 3.1 constants (same formulas and order of operations as documented in pf.h)
     s.lam = 3.0 * s.sigma * s.eta / (2.0 * std::sqrt(2.0));
     s.eps0 = scheme->eps0 != 0.0 ? scheme->eps0 : std::max(s.eps1, s.eps2);
@@ -1114,7 +1133,8 @@ int diag_impl(pf_handle *h, Engine<T> &E, double *out) {
     out[4] = h->v_iters;
     if (!(out[0] == out[0]) || !(um == um)) h->diverged = true;
     out[5] = h->diverged ? 1.0 : 0.0;
-    out[6] = out[7] = 0.0;
+    out[6] = E.reduce(E.phi[n], E.phi[1 - n], 2) / h->hs.dt;
+    out[7] = 0.0;
     return PF_OK;
 }
 
@@ -1324,7 +1344,7 @@ bool same_group(const HostSetup &a, const HostSetup &b) {
            a.rho2 == b.rho2 && a.mu1 == b.mu1 && a.mu2 == b.mu2 && a.sigma == b.sigma && a.eta == b.eta &&
            a.gamma1 == b.gamma1 && a.theta == b.theta && a.vrow0 == b.vrow0 && a.vrow1 == b.vrow1 &&
            a.dt == b.dt && a.bdf == b.bdf && a.precision == b.precision && a.S == b.S && a.nu_m == b.nu_m &&
-           a.rho0 == b.rho0;
+           a.rho0 == b.rho0 && a.model == b.model;
 }
 
 template <typename F>
@@ -1470,9 +1490,14 @@ extern "C" int pf_batch_umax(pf_batch *b, double *umax, double *mass) {
             const int B = (int)g.runs.size();
             std::vector<double> um(B, 0.0), t(B), m(B);
             for_engine(g, [&](auto &E) {
-                for (int c = 0; c < 2; ++c) {
-                    E.reduce_planes(E.u[c][E.cur], 1, t.data());
-                    for (int i = 0; i < B; ++i) um[i] = (t[i] != t[i] || um[i] != um[i]) ? NAN : std::max(um[i], t[i]);
+                if (g.hs.model == PF_MODEL_EQUILIBRIUM) {
+                    E.reduce_planes(E.phi[E.cur], 1, t.data(), E.phi[1 - E.cur]);
+                    for (int i = 0; i < B; ++i) um[i] = t[i] / g.hs.dt;
+                } else {
+                    for (int c = 0; c < 2; ++c) {
+                        E.reduce_planes(E.u[c][E.cur], 1, t.data());
+                        for (int i = 0; i < B; ++i) um[i] = (t[i] != t[i] || um[i] != um[i]) ? NAN : std::max(um[i], t[i]);
+                    }
                 }
                 if (mass) E.reduce_planes(E.phi[E.cur], 0, m.data());
             });

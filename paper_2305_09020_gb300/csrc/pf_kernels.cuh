@@ -21,7 +21,8 @@
 //   k_inv        inverse z FFT of a mode-plane solution (value and d/dz), Dirichlet
 //                values; variant for phi that also forms psi - alpha phi combinations
 //   k_gemm       C = A B with a small shared B (fast-diagonalisation transforms) and
-//                an epilogue that divides by the eigenvalue sum or stores transposed
+//                an epilogue that divides by the eigenvalue sum, stores transposed, or also
+//                writes -M C (the phi right-hand side of eq. 57 / 76 from psi)
 //   reductions   FP64 phase mass, max |u|, max |difference|
 #pragma once
 
@@ -540,6 +541,7 @@ __device__ __forceinline__ void plane_mode(int p, int nz, int &k, int &im) {
 
 template <typename T>
 struct FwdArgs {
+    long long cs_x0, cs_x1, cs_out; // strides between components (blockIdx.y), 0 for one
     const T *X0; int x0_local;      // input 0: element-local (1) or nodal (0)
     const T *X1; int x1_local;      // input 1 (nullable)
     int mult;                       // 0: X0 + i beta X1 ; 1: X0 + beta^2 M X1
@@ -587,6 +589,11 @@ __device__ __forceinline__ T gather4(const T *__restrict__ L, long long zoff, co
 
 template <typename T>
 __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
+    if (blockIdx.y) {   // component blockIdx.y of a batched launch
+        a.X0 += blockIdx.y * a.cs_x0;
+        if (a.X1) a.X1 += blockIdx.y * a.cs_x1;
+        a.out += blockIdx.y * a.cs_out;
+    }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
     const int nz = G.nz, ld = nz + 1, tp = a.tp;
@@ -668,6 +675,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
 
 template <typename T>
 struct InvArgs {
+    long long cs_y, cs_out; // strides between components (blockIdx.y), 0 for one
     const T *Y;          // packed mode planes of the solution (the plain variant's input)
     const T *psi;        // phi variant: packed psi modes
     const T *Q2h;        // phi variant: packed Q2 modes
@@ -697,6 +705,11 @@ __device__ __forceinline__ void put_pair(cplx<T> *x, int nz, int bits, int k, cp
 
 template <typename T>
 __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
+    if (blockIdx.y) {
+        a.Y += blockIdx.y * a.cs_y;
+        a.out += blockIdx.y * a.cs_out;
+        if (a.dzout) a.dzout += blockIdx.y * a.cs_out;
+    }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
     const int nz = G.nz, ld = nz + 1, tp = a.tp;
@@ -760,6 +773,7 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
 // is DSSUM'd nodal Q2 copied to out1 for the phi step)
 template <typename T>
 struct IndepFwd {
+    long long cs_x0, cs_out;   // strides between components (blockIdx.z)
     const T *X0;          // element-local
     const T *X1;          // nodal (copied to out1) or nullptr
     const T *scale_p;     // per-run scale or nullptr (then 1)
@@ -776,18 +790,19 @@ __global__ void k_fwd_indep(Geo<T> G, IndepFwd<T> a) {
     dss_sources(G, q, s);
     const long long lplane = (long long)G.ex * G.ey * G.p * G.p;
     const long long gi = (long long)p * G.n2 + q;
-    T v = gather4(a.X0, p * lplane, s);
+    T v = gather4(a.X0 + blockIdx.z * a.cs_x0, p * lplane, s);
     if (a.scale_p) v *= a.scale_p[p];
     if (a.liftb) {
         const int i = q / G.nx, j = q % G.nx;
         v -= (a.liftb[i] * a.vb_p[p] + a.liftt[i] * a.vt_p[p]) * G.Mx[j];
     }
-    a.out[gi] = v;
+    a.out[blockIdx.z * a.cs_out + gi] = v;
     if (a.out1) a.out1[gi] = a.X1[gi];
 }
 
 template <typename T>
 struct IndepInv {
+    long long cs_y, cs_out;   // strides between components (blockIdx.z)
     const T *Y;               // solution planes
     int drow0, drow1;         // Dirichlet rows (-1: none) receiving v0_p / v1_p
     const T *v0_p, *v1_p;
@@ -804,11 +819,11 @@ __global__ void k_inv_indep(Geo<T> G, IndepInv<T> a) {
     if (q >= G.n2) return;
     const int p = blockIdx.y;
     const long long gi = (long long)p * G.n2 + q;
-    T x = a.Y[gi];
+    T x = a.Y[blockIdx.z * a.cs_y + gi];
     const int i = q / G.nx;
     if (a.drow0 >= 0 && i == a.drow0) x += a.v0_p[p];
     if (a.drow1 >= 0 && i == a.drow1) x += a.v1_p[p];
-    a.out[gi] = x;
+    a.out[blockIdx.z * a.cs_out + gi] = x;
     if (a.outW) {
         const T ps = a.psi[gi];
         const T W = ps - (a.alpha + a.S_eta2) * x - a.Q2n[gi];
@@ -832,17 +847,18 @@ __global__ void k_face_indep(Geo<T> G, const T *__restrict__ face, T *__restrict
 
 // per-plane FP64 max |x| (or sum M x with kind 0), one block per plane
 template <typename T>
-__global__ void k_reduce_planes(const T *__restrict__ x, const T *__restrict__ Mx, const T *__restrict__ My,
-                                int nx, int n2, int kind, double *__restrict__ out) {
+__global__ void k_reduce_planes(const T *__restrict__ x, const T *__restrict__ y, const T *__restrict__ Mx,
+                                const T *__restrict__ My, int nx, int n2, int kind, double *__restrict__ out) {
     __shared__ double sm[256];
     const int p = blockIdx.x;
     const T *xp = x + (long long)p * n2;
+    const T *yp = y ? y + (long long)p * n2 : nullptr;
     double acc = 0.0;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         if (kind == 0) {
             acc += (double)Mx[i % nx] * (double)My[i / nx] * (double)xp[i];
         } else {
-            const double v = fabs((double)xp[i]);
+            const double v = yp ? fabs((double)xp[i] - (double)yp[i]) : fabs((double)xp[i]);
             if (acc == acc) {
                 if (v != v) acc = v;
                 else if (v > acc) acc = v;
@@ -859,20 +875,6 @@ __global__ void k_reduce_planes(const T *__restrict__ x, const T *__restrict__ M
         __syncthreads();
     }
     if (threadIdx.x == 0) out[p] = sm[0];
-}
-
-// right-hand side of eq. 57 / 76 in mode space: -M psi_hat (+ wall term rows)
-template <typename T>
-__global__ void k_rhs_phi(Geo<T> G, const T *__restrict__ psih, const T *__restrict__ faceh,
-                          T *__restrict__ out) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long tot = (long long)G.n2 * G.nz;
-    if (gid >= tot) return;
-    const int p = (int)(gid / G.n2), q = (int)(gid % G.n2);
-    const int i = q / G.nx, j = q % G.nx;
-    T v = -G.Mx[j] * G.My[i] * psih[gid];
-    if (faceh && i == 0) v += faceh[(long long)p * G.nx + j];
-    out[gid] = v;
 }
 
 // z-FFT of the wall face slots (direct stiffness summation along x first)
@@ -924,6 +926,10 @@ struct GemmArgs {
     int N, R, store;
     const T *lamN, *lamR, *cpl;
     int cpl_mod;   // plane index for cpl: p % cpl_mod
+    // optional second plain-store output C2 = -m2x[n] m2y[r] C (+ face2[p N + n] where r == 0):
+    // the phi right-hand side -M psi (+ wall term) written by the psi solve's last transform
+    T *C2;
+    const T *m2x, *m2y, *face2;
 };
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
@@ -1010,6 +1016,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
             }
             if (g.store == 0) g.C[m * g.N + n] = v;
             else g.C[(p * g.N + n) * g.R + r] = v;
+            if (g.C2) {
+                T w = -g.m2x[n] * g.m2y[r] * v;
+                if (g.face2 && r == 0) w += g.face2[p * g.N + n];
+                g.C2[m * g.N + n] = w;
+            }
         }
     }
 }

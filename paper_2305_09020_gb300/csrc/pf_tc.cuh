@@ -34,6 +34,8 @@ struct TcArgs {
     const float *lamN, *lamR, *cpl;
     int cpl_mod;
     int *err;                 // set to 1 when a bounded wait gives up
+    float *C2;                // optional: C2 = -m2x[n] m2y[r] C (+ face2[p N + n] on row r == 0)
+    const float *m2x, *m2y, *face2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -243,6 +245,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(TcArgs g) {
                     }
                     if (g.store == 0) g.C[m * g.N + n] = x;
                     else g.C[(p * g.N + n) * g.R + r] = x;
+                    if (g.C2) {
+                        float w2 = -g.m2x[n] * g.m2y[r] * x;
+                        if (g.face2 && r == 0) w2 += g.face2[p * g.N + n];
+                        g.C2[m * g.N + n] = w2;
+                    }
                 }
             }
         }

@@ -21,6 +21,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTSEPARABLE, PF_EDIVERGED, PF_ETIMEO
 PF_BC_DIRICHLET, PF_BC_NEUMANN = 0, 1
 PF_FP64, PF_MIXED, PF_MIXED_SIMT = 0, 1, 2
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
+PF_MODEL_FULL, PF_MODEL_EQUILIBRIUM = 0, 1
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64
 KERNEL_CLASSES = ["gemm", "fwd", "inv", "potential", "chem", "momentum", "ugradp", "efield", "other"]
@@ -50,7 +51,7 @@ class PfVbc(ctypes.Structure):
 
 class PfScheme(ctypes.Structure):
     _fields_ = [("dt", c_double), ("bdf", c_int), ("precision", c_int), ("S", c_double),
-                ("nu_m", c_double), ("rho0", c_double), ("eps0", c_double)]
+                ("nu_m", c_double), ("rho0", c_double), ("eps0", c_double), ("model", c_int)]
 
 
 _lib = None
@@ -197,7 +198,8 @@ class Solver:
                          float(vbc["v_top"]))
         self.scheme = PfScheme(float(scheme["dt"]), int(scheme.get("bdf", 2)), int(scheme.get("precision", PF_FP64)),
                                float(scheme.get("S", 0.0)), float(scheme.get("nu_m", 0.0)),
-                               float(scheme.get("rho0", 0.0)), float(scheme.get("eps0", 0.0)))
+                               float(scheme.get("rho0", 0.0)), float(scheme.get("eps0", 0.0)),
+                               int(scheme.get("model", PF_MODEL_FULL)))
         self.nx = self.mesh.ex * order
         self.ny = self.mesh.ey * order + 1
         self.nz = nz
@@ -304,7 +306,8 @@ def from_workload(wl, precision: int = PF_FP64, stream: Optional[int] = None, dt
                  eta=f.eta, gamma1=f.gamma1, theta_s_deg=f.theta_s_deg)
     vbc = dict(bottom_kind=v.bottom_kind, top_kind=v.top_kind, v_bottom=v.v_bottom, v_top=v.v_top)
     scheme = dict(dt=s.dt if dt is None else dt, bdf=s.bdf, precision=precision, S=s.S, nu_m=s.nu_m,
-                  rho0=s.rho0, eps0=s.eps0)
+                  rho0=s.rho0, eps0=s.eps0,
+                  model=PF_MODEL_EQUILIBRIUM if getattr(s, "equilibrium", False) else PF_MODEL_FULL)
     return Solver(m.xb, m.yb, m.order, m.nz, m.lz, fluid, vbc, scheme, phi0, stream=stream)
 
 
@@ -339,7 +342,8 @@ class Batch:
             vbcs[r] = PfVbc(v.bottom_kind, v.top_kind, v.v_bottom, v.v_top)
             phis[r] = _dp(phi)
             self.shapes.append((len(y), len(x)))
-        self.scheme = PfScheme(s0.dt, s0.bdf, int(precision), s0.S, s0.nu_m, s0.rho0, s0.eps0)
+        self.scheme = PfScheme(s0.dt, s0.bdf, int(precision), s0.S, s0.nu_m, s0.rho0, s0.eps0,
+                               PF_MODEL_EQUILIBRIUM if getattr(s0, "equilibrium", False) else PF_MODEL_FULL)
         h = c_void_p()
         _check(L.pf_batch_create(n, meshes, fluids, vbcs, ctypes.byref(self.scheme), phis, c_void_p(stream or 0),
                                  ctypes.byref(h)))

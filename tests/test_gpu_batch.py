@@ -87,3 +87,22 @@ def test_batch_run_to_equilibrium_reports_steps():
     steps = b.run_to_equilibrium(tol=0.0, max_steps=10, check_every=4)   # never below 0
     assert np.all(steps == -1)
     b.close()
+
+
+
+def test_batch_equilibrium_model_stops_on_rate():
+    runs = uneven_runs()
+    for w in runs:
+        w.scheme.equilibrium = True
+    b = native.Batch(runs, precision=native.PF_FP64)
+    oras = [solver_of(wl) for wl in runs]
+    b.step(4)
+    for o in oras:
+        for _ in range(4):
+            o.step()
+    _compare(b, runs, oras, 1e-11, 4)
+    rate, _ = b.umax()
+    for r, o in enumerate(oras):
+        ref = np.max(np.abs(o.phi - o.phi_old)) / o.prm.dt
+        assert abs(rate[r] - ref) <= 1e-9 * ref
+    b.close()

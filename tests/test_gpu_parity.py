@@ -138,3 +138,25 @@ def test_graph_replay_is_bit_identical(precision):
     b.close()
     for k in fa:
         assert np.array_equal(fa[k], fb[k]), k
+
+
+
+def test_equilibrium_model_parity_2d():
+    """Sec. 2.4 simpler system (u = 0; V and phi sub-steps only) against the oracle."""
+    wl = workloads.small2d(ex=4, ey=2, order=5, theta_s_deg=60.0)
+    wl.scheme.equilibrium = True
+    _assert_all(run_pair(wl, 8, check_every=4), FP64_TOL)
+
+
+def test_equilibrium_model_parity_3d_and_rate():
+    wl = workloads.small3d(ex=3, ey=2, order=5, nz=8)
+    wl.scheme.equilibrium = True
+    _assert_all(run_pair(wl, 5, check_every=5), FP64_TOL)
+    h = native.from_workload(wl, precision=native.PF_FP64)
+    h.step(3)
+    d = h.diagnostics()
+    f_old = h.get(native.PF_FIELD_PHI | native.PF_FIELD_OLD)["phi"]
+    f_new = h.get(native.PF_FIELD_PHI)["phi"]
+    h.close()
+    assert d[1] == 0.0                                           # u stays 0
+    assert abs(d[6] - np.max(np.abs(f_new - f_old)) / wl.scheme.dt) <= 1e-12 * d[6]

@@ -115,3 +115,51 @@ def test_fast_diagonalisation_equals_direct_solve(bc):
     ref = np.zeros(m.n2)
     ref[free] = spla.spsolve(A[free][:, free].tocsc(), (m.Mdiag * f.ravel())[free])
     np.testing.assert_allclose(u.ravel(), ref, atol=1e-12 * np.abs(ref).max())
+
+
+def _create(**over):
+    """pf_create with one descriptor field changed; the validation happens before any CUDA call."""
+    import ctypes
+    L = native.load()
+    xb = np.linspace(0, 2, 3)
+    yb = np.linspace(0, 1, 3)
+    m = dict(ex=2, ey=2, order=4, nz=1, lz=1.0)
+    m.update({k: v for k, v in over.items() if k in m})
+    xbv = np.ascontiguousarray(over.get("xb", xb), dtype=np.float64)
+    mesh = native.PfMesh(m["ex"], m["ey"], native._dp(xbv), native._dp(yb), m["order"], m["nz"], m["lz"])
+    fl = dict(rho1=1.0, rho2=1.0, mu1=1.0, mu2=1.0, eps1=2.0, eps2=1.0, sigma=1.0, eta=0.1, gamma1=1e-3,
+              theta_s_deg=90.0)
+    fl.update({k: v for k, v in over.items() if k in fl})
+    fluid = native.PfFluid(**fl)
+    vb = dict(bottom_kind=0, top_kind=0, v_bottom=1.0, v_top=0.0)
+    vb.update({k: v for k, v in over.items() if k in vb})
+    vbc = native.PfVbc(**vb)
+    sc = dict(dt=1e-3, bdf=2, precision=0, model=0)
+    sc.update({k: v for k, v in over.items() if k in sc})
+    scheme = native.PfScheme(sc["dt"], sc["bdf"], sc["precision"], 0.0, 0.0, 0.0, 0.0, sc.get("model", 0))
+    phi = np.zeros(10000)
+    h = ctypes.c_void_p()
+    rc = L.pf_create(ctypes.byref(mesh), ctypes.byref(fluid), ctypes.byref(vbc), ctypes.byref(scheme),
+                     native._dp(phi) if not over.get("null_phi") else None, None, None, ctypes.byref(h))
+    return rc, L.pf_last_error(None).decode(), h.value
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(order=1), "order"), (dict(order=16), "order"), (dict(nz=3), "nz"), (dict(nz=2048), "nz"),
+    (dict(ex=0), "element"), (dict(xb=np.array([0.0, 1.5, 1.0])), "xb"),
+    (dict(bottom_kind=1, top_kind=1), "electrode"), (dict(bottom_kind=7), "bottom_kind"),
+    (dict(dt=-1.0), "dt"), (dict(bdf=3), "bdf"), (dict(precision=9), "precision"),
+    (dict(eta=0.0), "positive"), (dict(model=5), "model"), (dict(rho2=-1.0), "positive"), (dict(null_phi=True), "null"),
+])
+def test_create_rejects_bad_descriptors_without_gpu(over, needle):
+    rc, msg, h = _create(**over)
+    assert rc == native.PF_EINVAL and h is None
+    assert needle in msg, msg
+
+
+def test_null_handles_are_rejected():
+    L = native.load()
+    assert L.pf_step(None, 1) == native.PF_EINVAL
+    assert L.pf_sync(None) == native.PF_EINVAL
+    assert L.pf_diagnostics(None, None) == native.PF_EINVAL
+    L.pf_destroy(None)          # no-op

@@ -193,3 +193,29 @@ def test_3d_z_independent_reduces_to_2d():
     for a, b in ((s2.V, s3.V), (s2.phi, s3.phi), (s2.P, s3.P), (s2.u[0], s3.u[0]), (s2.u[1], s3.u[1])):
         np.testing.assert_allclose(b, np.repeat(a, 4, axis=0), atol=1e-11)
     assert np.max(np.abs(s3.u[2])) < 1e-14
+
+
+def test_equilibrium_system_conserves_mass_and_keeps_u_zero():
+    """Sec. 2.4 simpler system: u = 0 throughout, so the phase-mass identity gives exact
+    conservation at every step (and the pseudo-time march lowers the free energy)."""
+    wl = workloads.small2d(ex=4, ey=2, order=6, theta_s_deg=60.0)
+    wl.scheme.equilibrium = True
+    sol = solver_of(wl)
+    m0 = sol.phase_mass()
+    for _ in range(8):
+        sol.step()
+        assert abs(sol.phase_mass() - m0) < 1e-13 * abs(m0)
+    assert sol.umax() == 0.0 and np.all(sol.P == 0.0)
+
+
+def test_equilibrium_system_matches_full_model_steps_for_phi_and_v():
+    """The simpler system's V and phi sub-steps are the full model's with u* = 0: on the
+    first step from rest (u^0 = 0) both give the same V^1 and phi^1."""
+    wl = workloads.small2d(ex=4, ey=2, order=5)
+    full = solver_of(wl)
+    wl.scheme.equilibrium = True
+    eq = solver_of(wl)
+    full.step()
+    eq.step()
+    np.testing.assert_allclose(eq.phi, full.phi, atol=1e-14)
+    np.testing.assert_allclose(eq.V, full.V, atol=1e-14)

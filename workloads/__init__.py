@@ -87,6 +87,7 @@ class Scheme:
     nu_m: float = 0.0       # 0 -> default max(mu)/min(rho)
     rho0: float = 0.0       # 0 -> default min(rho)
     eps0: float = 0.0       # 0 -> default max(eps)
+    equilibrium: bool = False   # march the simpler equilibrium system (u = 0) instead
 
 
 @dataclasses.dataclass
