@@ -214,8 +214,9 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
 
 /* Autotuner of a single run: time `steps` steady steps with each transform GEMM variant
  * (3xTF32 tensor cores where the precision has them, SIMT with 32x32 and 64x64 tiles), keep the
- * fastest, then (3D) the z-transform tile of 4, 8, 16 or 32 pencils per block.  The run
- * advances by 7 (steps + 1) steps (rounded up to even).  choice (nullable) receives
+ * fastest, then whether the y transforms run fused (one pass, eigenbasis in shared memory), then
+ * (3D) the z-transform tile of 4, 8, 16 or 32 pencils per block.  The run advances by
+ * 8 (steps + 1) steps (rounded up to even).  choice (nullable) receives
  * gemm + 1000 * tile, gemm = 0 for tensor cores or the SIMT tile 32 / 64, tile = 0 in 2D;
  * ms_per_step (nullable) the best time. */
 int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);

@@ -327,6 +327,9 @@ struct Engine {
         faceU = mk<T>((size_t)ex * p * nz);
         RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
+        if (fdm_y_smem() > 48 * 1024 && fdm_y_smem() <= 200 * 1024)
+            PF_CU(cudaFuncSetAttribute(pf::k_fdm_y<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fdm_y_smem()));
         red = mk<double>(std::max<long long>(1024, nz));
         dev_err = mk<int>(1);
         use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED;
@@ -433,7 +436,9 @@ struct Engine {
         if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;
         if (tp < 4) tp = 4;
-        return tp;
+        int p2 = 4;                  // a power of two: the kernels index with shifts and masks
+        while (p2 * 2 <= tp) p2 *= 2;
+        return p2;
     }
     void check_launch() { PF_CU(cudaGetLastError()); }
 
@@ -483,10 +488,26 @@ struct Engine {
     }
 
     // fast-diagonalisation solve of nplanes mode planes: out = S_y [ (S_y^T rhs S_x) / (L_y + L_x + c_p) ] S_x^T
+    // shared memory of the fused y pair (Sy, SyT, row block, intermediate)
+    size_t fdm_y_smem() const { return (size_t)(2 * ny * ny + 2 * 32 * ny) * sizeof(T); }
+    bool fuse_y = true;   // the autotuner may turn the fused y pair off
+
     void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
              const T *face = nullptr) {
         const long long P = nplanes;
         gemm(rhs, Sx, W1, P * ny, nx, ny, 1, nullptr, nullptr, nullptr, 1);
+        if (fuse_y && fdm_y_smem() <= 200 * 1024) {
+            // y transform, eigenvalue division and inverse y transform in one pass
+            constexpr int BM = 32, CG = 8;
+            const int threads = ((BM * ((ny + CG - 1) / CG) + 31) / 32) * 32;
+            prof->begin(PF_KC_GEMM, st);
+            pf::k_fdm_y<T, BM, CG><<<(unsigned)((P * nx + BM - 1) / BM), threads, fdm_y_smem(), st>>>(
+                W1, Sy[bcset], SyT[bcset], W2, P * nx, ny, nx, Ly[bcset], Lx, sh, nz);
+            check_launch();
+            prof->end(st);
+            gemm(W2, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1, minus_m_out, face);
+            return;
+        }
         gemm(W1, Sy[bcset], W2, P * nx, ny, nx, 0, Ly[bcset], Lx, sh, nz);
         gemm(W2, SyT[bcset], W1, P * nx, ny, nx, 1, nullptr, nullptr, nullptr, 1);
         gemm(W1, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1, minus_m_out, face);
@@ -525,7 +546,7 @@ struct Engine {
         a.S_eta2 = (T)(hs.S / std::pow(hs.eta, 2.0)); a.phi_variant = 1; a.drow0 = a.drow1 = -1;
         a.out = phi_out; a.dzout = d3 ? dzphi_out : nullptr; a.out2 = W; a.dzout2 = d3 ? dzW : nullptr;
         a.out3 = Lf; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz); a.tw = tw;
-        a.tp = std::max(4, fwd_tp() / 2);
+        a.tp = std::max(4, fwd_tp() / 2);    // still a power of two
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>);
         prof->begin(PF_KC_INV, st);
         pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
@@ -1241,6 +1262,20 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
     }
     E.use_tc = pick.tc;
     E.simt_tile = pick.tile;
+    // the fused y pair against the two separate y transforms
+    {
+        E.fuse_y = !E.fuse_y;
+        E.step(2);
+        PF_CU(cudaEventRecord(e0, E.st));
+        for (int s = 0; s < steps; ++s) E.step(2);
+        PF_CU(cudaEventRecord(e1, E.st));
+        PF_CU(cudaEventSynchronize(e1));
+        taken += steps + 1;
+        float ms = 0.f;
+        PF_CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / steps < best) best = ms / steps;
+        else E.fuse_y = !E.fuse_y;
+    }
     // then the transform tile (pencils per block), with the chosen GEMM
     if (E.d3) {
         int best_tp = 0;
@@ -1270,7 +1305,7 @@ extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_
     if (!h || steps < 1) return PF_EINVAL;
     try {
         if (h->nstep < 1) pf_step(h, 1);
-        int total = 7 * (steps + 1);
+        int total = 8 * (steps + 1);
         if (total % 2) total += 1;
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));

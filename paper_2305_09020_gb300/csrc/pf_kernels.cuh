@@ -510,17 +510,22 @@ __device__ __forceinline__ T dssum(const Geo<T> &G, const T *__restrict__ Lv, in
 // ---- in-shared-memory radix-2 FFT along z -------------------------------------------------
 __device__ __forceinline__ int bitrev(int v, int bits) { return bits ? (int)(__brev((unsigned)v) >> (32 - bits)) : 0; }
 
-// in-place DIT FFT of npen pencils of length n (bit-reversed input), sign -1 forward / +1 inverse
+// in-place DIT FFT of npen pencils of length n = 2^lg (bit-reversed input), forward or inverse;
+// all index arithmetic is shifts and masks (n, the spans and the pencil count are powers of two
+// or plain multiples)
 template <typename T>
 __device__ void fft_pencils(cplx<T> *buf, int ld, int npen, int n, const cplx<T> *tw, bool inverse) {
-    for (int len = 2; len <= n; len <<= 1) {
-        const int half = len >> 1, stride = n / len;
-        const int nb = npen * (n >> 1);
+    const int lg = 31 - __clz(n);
+    const int hb = lg - 1;                       // log2(n / 2)
+    const int nb = npen << hb;
+    for (int s = 1; s <= lg; ++s) {
+        const int hs = s - 1;                    // log2(half span)
+        const int hmask = (1 << hs) - 1;
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int pen = t / (n >> 1), bf = t % (n >> 1);
-            const int grp = bf / half, jj = bf % half;
-            const int i0 = grp * len + jj, i1 = i0 + half;
-            cplx<T> w = tw[jj * stride];
+            const int pen = t >> hb, bf = t & ((1 << hb) - 1);
+            const int grp = bf >> hs, jj = bf & hmask;
+            const int i0 = (grp << s) + jj, i1 = i0 + (1 << hs);
+            cplx<T> w = tw[jj << (lg - s)];
             if (inverse) w.y = -w.y;
             cplx<T> *x = buf + pen * ld;
             const cplx<T> u = x[i0];
@@ -610,6 +615,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     __syncthreads();
     const long long lplane = (long long)G.ex * G.ey * G.p * G.p;
     const int total = tp * nz;
+    const int lgtp = 31 - __clz(tp);          // tp is a power of two
     for (int base = threadIdx.x; base < total; base += 4 * blockDim.x) {
         T v0[4], v1[4];
 #pragma unroll
@@ -618,7 +624,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
             v0[u] = 0;
             v1[u] = 0;
             if (idx < total) {
-                const int z = idx / tp, ql = idx - z * tp, qg = q0 + ql;
+                const int z = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
                 if (qg < G.n2) {
                     const long long gi = (long long)z * G.n2 + qg;
                     const int *s = ssrc + ql * 4;
@@ -631,7 +637,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
         for (int u = 0; u < 4; ++u) {
             const int idx = base + u * blockDim.x;
             if (idx < total) {
-                const int z = idx / tp, ql = idx - z * tp;
+                const int z = idx >> lgtp, ql = idx & (tp - 1);
                 buf[ql * ld + bitrev(z, bits)] = {v0[u], v1[u]};
             }
         }
@@ -640,7 +646,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
     const T inv_n = T(1) / T(nz);
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
-        const int p = idx / tp, ql = idx % tp, qg = q0 + ql;
+        const int p = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
         if (qg >= G.n2) continue;
         int k, im;
         plane_mode(p, nz, k, im);
@@ -720,8 +726,9 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     const int q0 = blockIdx.x * tp;
     // load the half spectra: one (k) per thread-iteration, both Re and Im planes
     const int nk = nz / 2 + 1;
+    const int lgtp = 31 - __clz(tp);          // tp is a power of two
     for (int idx = threadIdx.x; idx < tp * (nz > 1 ? nk : 1); idx += blockDim.x) {
-        const int k = idx / tp, ql = idx % tp, qg = q0 + ql;
+        const int k = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
         cplx<T> X = {0, 0}, Wk = {0, 0};
         if (qg < G.n2) {
             int pre, pim;
@@ -753,7 +760,7 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     __syncthreads();
     if (nz > 1) fft_pencils(buf, ld, tp * npair, nz, stw, true);
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
-        const int z = idx / tp, ql = idx % tp, qg = q0 + ql;
+        const int z = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
         if (qg >= G.n2) continue;
         const long long gi = (long long)z * G.n2 + qg;
         const cplx<T> r = buf[ql * ld + z];
@@ -888,8 +895,9 @@ __global__ void k_face_fft(Geo<T> G, const T *__restrict__ face, T *__restrict__
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = tw[i];
     const int j0 = blockIdx.x * tp;
+    const int lgtp = 31 - __clz(tp);          // tp is a power of two
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
-        const int z = idx / tp, jl = idx % tp, j = j0 + jl;
+        const int z = idx >> lgtp, jl = idx & (tp - 1), j = j0 + jl;
         T v = 0;
         if (j < G.nx) {
             const int K = G.K, p = G.p;
@@ -906,7 +914,7 @@ __global__ void k_face_fft(Geo<T> G, const T *__restrict__ face, T *__restrict__
     if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
     const T inv_n = T(1) / T(nz);
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
-        const int p = idx / tp, jl = idx % tp, j = j0 + jl;
+        const int p = idx >> lgtp, jl = idx & (tp - 1), j = j0 + jl;
         if (j >= G.nx) continue;
         int k, im;
         plane_mode(p, nz, k, im);
@@ -1022,6 +1030,78 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
                 g.C2[m * g.N + n] = w;
             }
         }
+    }
+}
+
+// ---- fused y-direction pair of a fast-diagonalisation solve ------------------------------------
+// For BM rows of A (rows m = p R + r, length ny): t = A_m Sy, t /= (lamN[n] + lamR[r] + cpl[p]),
+// out = t SyT stored transposed within planes: C[p][n][r].  Sy, SyT, the row block and t stay in
+// shared memory; thread (row, column group of CG columns).  Used when 2 ny^2 + 2 BM ny values fit.
+template <typename T, int BM, int CG>
+__global__ void k_fdm_y(const T *__restrict__ A, const T *__restrict__ Sy, const T *__restrict__ SyT,
+                        T *__restrict__ C, long long Mrows, int ny, int R, const T *__restrict__ lamN,
+                        const T *__restrict__ lamR, const T *__restrict__ cpl, int cpl_mod) {
+    extern __shared__ unsigned char pf_smem_raw[];
+    T *sS = reinterpret_cast<T *>(pf_smem_raw);    // ny x ny
+    T *sST = sS + ny * ny;                         // ny x ny
+    T *sA = sST + ny * ny;                         // BM x ny
+    T *sT = sA + BM * ny;                          // BM x ny
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const long long m0 = (long long)blockIdx.x * BM;
+    for (int i = tid; i < ny * ny; i += nth) {
+        sS[i] = Sy[i];
+        sST[i] = SyT[i];
+    }
+    for (int i = tid; i < BM * ny; i += nth) {
+        const long long m = m0 + i / ny;
+        sA[i] = m < Mrows ? A[m0 * ny + i] : T(0);
+    }
+    __syncthreads();
+    const int ngrp = (ny + CG - 1) / CG;
+    const int row = tid / ngrp, grp = tid - row * ngrp;
+    const bool act = row < BM;
+    const int c0 = grp * CG;
+    const long long m = m0 + row;
+    long long p = 0;
+    int r = 0;
+    if (act && m < Mrows) {
+        p = m / R;
+        r = (int)(m - p * R);
+    }
+    T acc[CG];
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[j] = 0;
+        for (int i = 0; i < ny; ++i) {
+            const T a = sA[row * ny + i];
+#pragma unroll
+            for (int j = 0; j < CG; ++j)
+                if (c0 + j < ny) acc[j] += a * sS[i * ny + c0 + j];
+        }
+        const T base = lamR[r] + cpl[p % cpl_mod];
+#pragma unroll
+        for (int j = 0; j < CG; ++j) {
+            const int n = c0 + j;
+            if (n < ny) {
+                const T d = lamN[n] + base;
+                sT[row * ny + n] = (d != T(0)) ? acc[j] / d : T(0);
+            }
+        }
+    }
+    __syncthreads();
+    if (!act || m >= Mrows) return;
+#pragma unroll
+    for (int j = 0; j < CG; ++j) acc[j] = 0;
+    for (int i = 0; i < ny; ++i) {
+        const T t = sT[row * ny + i];
+#pragma unroll
+        for (int j = 0; j < CG; ++j)
+            if (c0 + j < ny) acc[j] += t * sST[i * ny + c0 + j];
+    }
+#pragma unroll
+    for (int j = 0; j < CG; ++j) {
+        const int n = c0 + j;
+        if (n < ny) C[(p * ny + n) * R + r] = acc[j];
     }
 }
 
