@@ -317,7 +317,8 @@ def main():
                                    "electrode, eps/rho/mu ratios 10/2/5, V=2, dt=5e-5",
                        "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
-                       "fdm_gemm": {0: "tcgen05 3xTF32"}.get(gemm_choice, f"SIMT {gemm_choice}x{gemm_choice} tiles")
+                       "fdm_gemm": {0: "tcgen05 3xTF32", 1: "whole solve per plane in shared memory (SIMT)",
+                                    2: "SIMT 32x64 tiles"}.get(gemm_choice, f"SIMT {gemm_choice}x{gemm_choice} tiles")
                                    + " (autotuned)",
                        "fft_pencils_per_block": fft_tile,
                        "parallelism": f"replicas x{world}"},

@@ -330,6 +330,15 @@ struct Engine {
         if (fdm_y_smem() > 48 * 1024 && fdm_y_smem() <= 200 * 1024)
             PF_CU(cudaFuncSetAttribute(pf::k_fdm_y<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fdm_y_smem()));
+        if constexpr (sizeof(T) == 4) {
+            if (plane_fits()) {   // opt in once, before any graph capture
+                const int cq = plane_cq();
+                const void *fn = cq == 1 ? (const void *)pf::k_fdm_plane<1>
+                                 : cq == 2 ? (const void *)pf::k_fdm_plane<2> : (const void *)pf::k_fdm_plane<4>;
+                PF_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fdm_plane_smem()));
+            }
+        }
+
         red = mk<double>(std::max<long long>(1024, nz));
         dev_err = mk<int>(1);
         use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED;
@@ -475,7 +484,10 @@ struct Engine {
         const long long tiles64 = ((Ncol + 63) / 64) * ((Mrows + 63) / 64);
         prof->begin(PF_KC_GEMM, st);
         const bool big = simt_tile == 64 || (simt_tile == 0 && tiles64 >= 4 * 152 && Ncol % 64 > 32);
-        if (big) {
+        if (simt_tile == 2) {   // 32x64 tiles
+            dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 31) / 32));
+            pf::k_gemm<T, 32, 64, BK, 2, 4><<<grid, 256, 0, st>>>(g);
+        } else if (big) {
             dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 63) / 64));
             pf::k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(g);
         } else {
@@ -491,10 +503,38 @@ struct Engine {
     // shared memory of the fused y pair (Sy, SyT, row block, intermediate)
     size_t fdm_y_smem() const { return (size_t)(2 * ny * ny + 2 * 32 * ny) * sizeof(T); }
     bool fuse_y = true;   // the autotuner may turn the fused y pair off
+    // the whole-plane solve (FP32 only): columns per lane, shared memory (Sx, Sy, one plane)
+    int plane_cq() const { return nx <= 32 ? 1 : nx <= 64 ? 2 : 4; }
+    size_t fdm_plane_smem() const {
+        const size_t nxp = 32 * plane_cq(), nyp = pf::fdm_plane_nyp(ny);
+        return (nxp * nxp + nyp * nyp + nyp * nxp) * sizeof(float);
+    }
+    bool plane_fits() const {
+        return sizeof(T) == 4 && nx <= 128 && ny <= 128 && fdm_plane_smem() <= 227 * 1024;
+    }
+    bool fuse_plane = false;   // chosen by the autotuner when it is faster
+    template <int CQ>
+    void launch_plane(const T *rhs, T *out, int bcset, const T *sh, long long P, T *c2, const T *face) {
+        if constexpr (sizeof(T) == 4) {
+            const unsigned threads = 32u * (unsigned)(pf::fdm_plane_nyp(ny) / 8);
+            pf::k_fdm_plane<CQ><<<(unsigned)P, threads, fdm_plane_smem(), st>>>(
+                rhs, out, nx, ny, Sx, Sy[bcset], Lx, Ly[bcset], sh, nz, c2, Mx, My, face);
+        }
+    }
 
     void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
              const T *face = nullptr) {
         const long long P = nplanes;
+        if (fuse_plane && plane_fits()) {
+            prof->begin(PF_KC_GEMM, st);
+            const int cq = plane_cq();
+            if (cq == 1) launch_plane<1>(rhs, out, bcset, sh, P, minus_m_out, face);
+            else if (cq == 2) launch_plane<2>(rhs, out, bcset, sh, P, minus_m_out, face);
+            else launch_plane<4>(rhs, out, bcset, sh, P, minus_m_out, face);
+            check_launch();
+            prof->end(st);
+            return;
+        }
         gemm(rhs, Sx, W1, P * ny, nx, ny, 1, nullptr, nullptr, nullptr, 1);
         if (fuse_y && fdm_y_smem() <= 200 * 1024) {
             // y transform, eigenvalue division and inverse y transform in one pass
@@ -1236,44 +1276,58 @@ extern "C" int pf_profile_read(pf_handle *h, double *ms, long long *launches) {
 }
 
 namespace {
-// time `steps` steady steps of each transform variant, keep the fastest; advances `total` steps
+// time `steps` steady steps of each transform variant, keep the fastest; advances `total` steps.
+// Steps run as the run will run them: replays of the captured graphs on a non-default stream
+// (re-captured for every variant), eager launches on the legacy stream.
 template <typename T>
 void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEvent_t e1, int *choice, double *best_ms) {
+    auto drop_graphs = [&]() {
+        for (int c = 0; c < 2; ++c)
+            if (E.graph[c]) { cudaGraphExecDestroy(E.graph[c]); E.graph[c] = nullptr; }
+    };
+    auto one = [&]() {
+        if (E.st != nullptr && !E.prof->on) E.step_graph();
+        else E.step(2);
+    };
+    // two untimed steps (both history parities captured), then `steps` timed ones
+    auto time_variant = [&](int &taken) {
+        drop_graphs();
+        one();
+        one();
+        PF_CU(cudaEventRecord(e0, E.st));
+        for (int s = 0; s < steps; ++s) one();
+        PF_CU(cudaEventRecord(e1, E.st));
+        PF_CU(cudaEventSynchronize(e1));
+        taken += steps + 2;
+        float ms = 0.f;
+        PF_CU(cudaEventElapsedTime(&ms, e0, e1));
+        return (double)ms / steps;
+    };
     struct Cand { bool tc; int tile; };
     std::vector<Cand> cands;
     if (!E.tcb.empty()) cands.push_back({true, 0});
     cands.push_back({false, 32});
     cands.push_back({false, 64});
+    cands.push_back({false, 2});
+    if (E.plane_fits()) cands.push_back({false, -1});   // whole solve per plane in shared memory
     Cand pick = cands[0];
     double best = INFINITY;
     int taken = 0;
     for (const Cand &c : cands) {
         E.use_tc = c.tc;
-        E.simt_tile = c.tile;
-        E.step(2);
-        PF_CU(cudaEventRecord(e0, E.st));
-        for (int s = 0; s < steps; ++s) E.step(2);
-        PF_CU(cudaEventRecord(e1, E.st));
-        PF_CU(cudaEventSynchronize(e1));
-        taken += steps + 1;
-        float ms = 0.f;
-        PF_CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms / steps < best) { best = ms / steps; pick = c; }
+        E.simt_tile = c.tile < 0 ? 0 : c.tile;
+        E.fuse_plane = c.tile < 0;
+        const double ms = time_variant(taken);
+        if (ms < best) { best = ms; pick = c; }
     }
     E.use_tc = pick.tc;
-    E.simt_tile = pick.tile;
+    E.simt_tile = pick.tile < 0 ? 0 : pick.tile;
+    E.fuse_plane = pick.tile < 0;
     // the fused y pair against the two separate y transforms
-    {
+    if (!E.fuse_plane) {
         E.fuse_y = !E.fuse_y;
-        E.step(2);
-        PF_CU(cudaEventRecord(e0, E.st));
-        for (int s = 0; s < steps; ++s) E.step(2);
-        PF_CU(cudaEventRecord(e1, E.st));
-        PF_CU(cudaEventSynchronize(e1));
-        taken += steps + 1;
-        float ms = 0.f;
-        PF_CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms / steps < best) best = ms / steps;
+        const double ms = time_variant(taken);
+        if (ms < best) best = ms;
         else E.fuse_y = !E.fuse_y;
     }
     // then the transform tile (pencils per block), with the chosen GEMM
@@ -1281,22 +1335,14 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
         int best_tp = 0;
         for (int tp : {4, 8, 16, 32}) {
             E.tp_override = tp;
-            E.step(2);
-            PF_CU(cudaEventRecord(e0, E.st));
-            for (int s = 0; s < steps; ++s) E.step(2);
-            PF_CU(cudaEventRecord(e1, E.st));
-            PF_CU(cudaEventSynchronize(e1));
-            taken += steps + 1;
-            float ms = 0.f;
-            PF_CU(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms / steps < best) { best = ms / steps; best_tp = tp; }
+            const double ms = time_variant(taken);
+            if (ms < best) { best = ms; best_tp = tp; }
         }
         E.tp_override = best_tp;
     }
+    drop_graphs();
     for (; taken < total; ++taken) E.step(2);
-    for (int c = 0; c < 2; ++c)
-        if (E.graph[c]) { cudaGraphExecDestroy(E.graph[c]); E.graph[c] = nullptr; }
-    if (choice) *choice = (pick.tc ? 0 : pick.tile) + 1000 * E.tp_override;
+    if (choice) *choice = (pick.tc ? 0 : (pick.tile < 0 ? 1 : pick.tile)) + 1000 * E.tp_override;
     if (best_ms) *best_ms = best;
 }
 }  // namespace
@@ -1305,8 +1351,7 @@ extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_
     if (!h || steps < 1) return PF_EINVAL;
     try {
         if (h->nstep < 1) pf_step(h, 1);
-        int total = 8 * (steps + 1);
-        if (total % 2) total += 1;
+        int total = 10 * (steps + 2);   // at most 5 GEMM variants + the y pair + 4 tiles
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));
         PF_CU(cudaEventCreate(&e1));
@@ -1317,6 +1362,40 @@ extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_
         h->nstep += total;
         h->t += total * h->hs.dt;
         h->last_J = 2;
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+    return PF_OK;
+}
+
+namespace {
+// pin the transform variants of one engine; false when the engine cannot use them
+template <typename T>
+bool set_variant(Engine<T> &E, int gemm, int fuse_y, int tile) {
+    const bool gemm_ok = (gemm == 0 && !E.tcb.empty()) || (gemm == 1 && E.plane_fits()) || gemm == 32 ||
+                         gemm == 64 || gemm == 2;
+    const bool tile_ok = tile == 0 || tile == 4 || tile == 8 || tile == 16 || tile == 32;
+    if (!gemm_ok || (fuse_y != 0 && fuse_y != 1) || !tile_ok) return false;
+    E.use_tc = gemm == 0;
+    E.fuse_plane = gemm == 1;
+    E.simt_tile = gemm >= 2 ? gemm : 0;
+    E.fuse_y = fuse_y == 1;
+    E.tp_override = tile;
+    for (int c = 0; c < 2; ++c)
+        if (E.graph[c]) { cudaGraphExecDestroy(E.graph[c]); E.graph[c] = nullptr; }
+    return true;
+}
+}  // namespace
+
+extern "C" int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile) {
+    if (!h) return PF_EINVAL;
+    try {
+        PF_CU(cudaStreamSynchronize(h->st));
+        const bool ok = h->e64 ? set_variant(*h->e64, gemm, fuse_y, tile) : set_variant(*h->e32, gemm, fuse_y, tile);
+        if (!ok) {
+            h->err = "pf_set_variant: variant not available for this run";
+            return PF_EINVAL;
+        }
     } catch (const CudaError &e) {
         return cuda_fail(h, e);
     }
@@ -1621,6 +1700,27 @@ extern "C" int pf_batch_get_fields(pf_batch *b, int run, unsigned mask, double *
     return PF_OK;
 }
 
+extern "C" int pf_batch_set_variant(pf_batch *b, int gemm, int fuse_y) {
+    if (!b) return PF_EINVAL;
+    try {
+        PF_CU(cudaStreamSynchronize(b->st));
+        for (auto &gp : b->groups) {   // every group must be able to take the variant
+            bool ok = true;
+            for_engine(*gp, [&](auto &E) {
+                ok = (gemm == 0 && !E.tcb.empty()) || (gemm == 1 && E.plane_fits()) || gemm == 32 || gemm == 64 ||
+                     gemm == 2;
+            });
+            if (!ok || (fuse_y != 0 && fuse_y != 1))
+                return batch_fail(b, PF_EINVAL, "pf_batch_set_variant: variant not available for every group");
+        }
+        for (auto &gp : b->groups) for_engine(*gp, [&](auto &E) { set_variant(E, gemm, fuse_y, 0); });
+        batch_invalidate_graphs(b);
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return PF_OK;
+}
+
 extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
     if (!b || steps < 1) return PF_EINVAL;
     try {
@@ -1629,9 +1729,9 @@ extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));
         PF_CU(cudaEventCreate(&e1));
-        // every group takes the same number of steps (3 variants x (steps + 1), rounded up to an
+        // every group takes the same number of steps (4 variants x (steps + 1), rounded up to an
         // even count so the history-slot parity of all groups stays equal)
-        int total = 3 * (steps + 1);
+        int total = 4 * (steps + 1);
         if (total % 2) total += 1;
         for (size_t gi = 0; gi < b->groups.size(); ++gi) {
             auto &g = *b->groups[gi];
@@ -1642,11 +1742,13 @@ extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
                 if (!E.tcb.empty()) cands.push_back({true, 0});
                 cands.push_back({false, 32});
                 cands.push_back({false, 64});
+                if (E.plane_fits()) cands.push_back({false, -1});
                 Cand pick = cands[0];
                 int taken = 0;
                 for (const Cand &c : cands) {
                     E.use_tc = c.tc;
-                    E.simt_tile = c.tile;
+                    E.simt_tile = c.tile < 0 ? 0 : c.tile;
+                    E.fuse_plane = c.tile < 0;
                     E.step(2);   // warm-up of this variant
                     PF_CU(cudaEventRecord(e0, E.st));
                     for (int s = 0; s < steps; ++s) E.step(2);
@@ -1658,7 +1760,8 @@ extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
                     if (ms / steps < best) { best = ms / steps; pick = c; }
                 }
                 E.use_tc = pick.tc;
-                E.simt_tile = pick.tile;
+                E.simt_tile = pick.tile < 0 ? 0 : pick.tile;
+                E.fuse_plane = pick.tile < 0;
                 for (; taken < total; ++taken) E.step(2);
             });
             if (ms_out) ms_out[gi] = best;

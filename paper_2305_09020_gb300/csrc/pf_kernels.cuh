@@ -951,11 +951,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
     const long long m0 = (long long)blockIdx.y * BM;
     const int n0 = blockIdx.x * BN;
-    T acc[TM][TN];
+    // blocked summation: in FP32 each k tile is summed into `part` and then added to `acc` (the
+    // rounding error of a length-n dot product grows with the block length plus the number of
+    // blocks instead of n); in FP64 the whole k range is one block, i.e. plain sequential order
+    T acc[TM][TN], part[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+        for (int j = 0; j < TN; ++j) acc[i][j] = part[i][j] = 0;
     T ra_[LA], rb_[LB];
     auto fetch = [&](int k0) {   // all loads of one k tile issued back to back
 #pragma unroll
@@ -1001,7 +1004,16 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] += ra[i] * rb[j];
+                for (int j = 0; j < TN; ++j) part[i][j] += ra[i] * rb[j];
+        }
+        if (sizeof(T) == 4 || !more) {
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    acc[i][j] += part[i][j];
+                    part[i][j] = 0;
+                }
         }
         if (more) put(buf ^ 1);
         __syncthreads();
@@ -1033,6 +1045,25 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
     }
 }
 
+// dst(t, src(t)) for t < n by the whole block, U independent global loads in flight per thread
+// before their shared-memory stores (a plain strided loop waits on each load in turn)
+template <int U, typename T, typename Src, typename Dst>
+__device__ __forceinline__ void block_stage(int n, Src src, Dst dst) {
+    for (int t0 = threadIdx.x; t0 < n; t0 += U * blockDim.x) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * (int)blockDim.x;
+            v[u] = t < n ? src(t) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u * (int)blockDim.x;
+            if (t < n) dst(t, v[u]);
+        }
+    }
+}
+
 // ---- fused y-direction pair of a fast-diagonalisation solve ------------------------------------
 // For BM rows of A (rows m = p R + r, length ny): t = A_m Sy, t /= (lamN[n] + lamR[r] + cpl[p]),
 // out = t SyT stored transposed within planes: C[p][n][r].  Sy, SyT, the row block and t stay in
@@ -1046,16 +1077,12 @@ __global__ void k_fdm_y(const T *__restrict__ A, const T *__restrict__ Sy, const
     T *sST = sS + ny * ny;                         // ny x ny
     T *sA = sST + ny * ny;                         // BM x ny
     T *sT = sA + BM * ny;                          // BM x ny
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x;
     const long long m0 = (long long)blockIdx.x * BM;
-    for (int i = tid; i < ny * ny; i += nth) {
-        sS[i] = Sy[i];
-        sST[i] = SyT[i];
-    }
-    for (int i = tid; i < BM * ny; i += nth) {
-        const long long m = m0 + i / ny;
-        sA[i] = m < Mrows ? A[m0 * ny + i] : T(0);
-    }
+    block_stage<8, T>(ny * ny, [&](int i) { return Sy[i]; }, [&](int i, T v) { sS[i] = v; });
+    block_stage<8, T>(ny * ny, [&](int i) { return SyT[i]; }, [&](int i, T v) { sST[i] = v; });
+    block_stage<8, T>(BM * ny, [&](int i) { return m0 + i / ny < Mrows ? A[m0 * ny + i] : T(0); },
+                      [&](int i, T v) { sA[i] = v; });
     __syncthreads();
     const int ngrp = (ny + CG - 1) / CG;
     const int row = tid / ngrp, grp = tid - row * ngrp;
@@ -1068,15 +1095,24 @@ __global__ void k_fdm_y(const T *__restrict__ A, const T *__restrict__ Sy, const
         p = m / R;
         r = (int)(m - p * R);
     }
-    T acc[CG];
+    // blocked summation as in k_gemm: blocks of 16 terms in FP32, one block in FP64
+    constexpr int KB = sizeof(T) == 4 ? 16 : (1 << 30);
+    T acc[CG], part[CG];
     if (act) {
 #pragma unroll
         for (int j = 0; j < CG; ++j) acc[j] = 0;
-        for (int i = 0; i < ny; ++i) {
-            const T a = sA[row * ny + i];
+        for (int i0 = 0; i0 < ny; i0 += KB) {
 #pragma unroll
-            for (int j = 0; j < CG; ++j)
-                if (c0 + j < ny) acc[j] += a * sS[i * ny + c0 + j];
+            for (int j = 0; j < CG; ++j) part[j] = 0;
+            const int i1 = min(ny, i0 + KB);
+            for (int i = i0; i < i1; ++i) {
+                const T a = sA[row * ny + i];
+#pragma unroll
+                for (int j = 0; j < CG; ++j)
+                    if (c0 + j < ny) part[j] += a * sS[i * ny + c0 + j];
+            }
+#pragma unroll
+            for (int j = 0; j < CG; ++j) acc[j] += part[j];
         }
         const T base = lamR[r] + cpl[p % cpl_mod];
 #pragma unroll
@@ -1092,16 +1128,174 @@ __global__ void k_fdm_y(const T *__restrict__ A, const T *__restrict__ Sy, const
     if (!act || m >= Mrows) return;
 #pragma unroll
     for (int j = 0; j < CG; ++j) acc[j] = 0;
-    for (int i = 0; i < ny; ++i) {
-        const T t = sT[row * ny + i];
+    for (int i0 = 0; i0 < ny; i0 += KB) {
 #pragma unroll
-        for (int j = 0; j < CG; ++j)
-            if (c0 + j < ny) acc[j] += t * sST[i * ny + c0 + j];
+        for (int j = 0; j < CG; ++j) part[j] = 0;
+        const int i1 = min(ny, i0 + KB);
+        for (int i = i0; i < i1; ++i) {
+            const T t = sT[row * ny + i];
+#pragma unroll
+            for (int j = 0; j < CG; ++j)
+                if (c0 + j < ny) part[j] += t * sST[i * ny + c0 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[j] += part[j];
     }
 #pragma unroll
     for (int j = 0; j < CG; ++j) {
         const int n = c0 + j;
         if (n < ny) C[(p * ny + n) * R + r] = acc[j];
+    }
+}
+
+// ---- a whole fast-diagonalisation solve per mode plane, in shared memory ----------------------
+// out[p] = Sy [ (Sy^T rhs[p] Sx) / (Ly + Lx + c_p) ] Sx^T for plane p = blockIdx.x (FP32), with the
+// optional second output C2 = -Mx My out (+ face2 on row 0) of the psi solve.  The plane stays in
+// shared memory through the four transforms.  Warp w owns rows 8w..8w+7 of each stage's output, lane
+// l the columns l + 32q (q < CQ), so the per-lane operand is read without bank conflicts and the
+// per-warp operand is a broadcast (four k at a time where it is a row).  Sx is stored with its
+// columns XOR-swizzled by the row (c ^ (r & 31)) so that its rows (x stage) and its columns (x^T
+// stage) are both conflict-free.  Shared layout (floats): Sx nxp^2, Sy nyp^2, plane nyp x nxp, with
+// nxp = 32 CQ and nyp = ny rounded up to 8; the padding is zero.
+__host__ __device__ constexpr int fdm_plane_nyp(int ny) { return (ny + 7) & ~7; }
+
+template <int CQ>
+__global__ void __launch_bounds__(512) k_fdm_plane(const float *__restrict__ rhs, float *__restrict__ out, int nx,
+                                                     int ny, const float *__restrict__ Sx,
+                                                     const float *__restrict__ Sy, const float *__restrict__ Lx,
+                                                     const float *__restrict__ Ly, const float *__restrict__ cpl,
+                                                     int cpl_mod, float *__restrict__ C2,
+                                                     const float *__restrict__ Mx, const float *__restrict__ My,
+                                                     const float *__restrict__ face2) {
+    constexpr int NXP = 32 * CQ, RW = 8;
+    extern __shared__ __align__(16) unsigned char pf_smem_raw[];
+    const int nyp = fdm_plane_nyp(ny);
+    float *sSx = reinterpret_cast<float *>(pf_smem_raw);
+    float *sSy = sSx + NXP * NXP;
+    float *pl = sSy + nyp * nyp;
+    const int p = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, i0 = RW * w;
+    const long long n2 = (long long)nx * ny;
+    block_stage<8, float>(
+        NXP * NXP, [&](int t) { const int r = t / NXP, c = t % NXP; return (r < nx && c < nx) ? Sx[r * nx + c] : 0.f; },
+        [&](int t, float v) { const int r = t / NXP, c = t % NXP; sSx[r * NXP + (c ^ (r & 31))] = v; });
+    block_stage<8, float>(
+        nyp * nyp, [&](int t) { const int r = t / nyp, c = t - r * nyp; return (r < ny && c < ny) ? Sy[r * ny + c] : 0.f; },
+        [&](int t, float v) { sSy[t] = v; });
+    block_stage<8, float>(
+        nyp * NXP,
+        [&](int t) {
+            const int r = t / NXP, c = t % NXP;
+            return (r < ny && c < nx) ? rhs[p * n2 + (long long)r * nx + c] : 0.f;
+        },
+        [&](int t, float v) { pl[t] = v; });
+    __syncthreads();
+    // blocked summation: each block of 16 k is summed into `part`, then added to `acc`
+    constexpr int KB = 16;
+    float acc[RW][CQ], part[RW][CQ];
+    auto zero = [&](float (&x)[RW][CQ]) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) x[r][q] = 0.f;
+    };
+    auto flush = [&]() {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                acc[r][q] += part[r][q];
+                part[r][q] = 0.f;
+            }
+    };
+    // acc = (rows i0.. of) L R, L row-major in shared memory with leading dimension ldl (a multiple
+    // of 4) read four k at a time; R(k, j) given by rk
+    auto rows_times = [&](const float *L, int ldl, int kdim, auto rk) {
+        zero(acc);
+        zero(part);
+        for (int k0 = 0; k0 < kdim; k0 += 4) {
+            if (k0 > 0 && k0 % KB == 0) flush();
+            float4 a[RW];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) a[r] = *reinterpret_cast<const float4 *>(L + (i0 + r) * ldl + k0);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float b[CQ];
+#pragma unroll
+                for (int q = 0; q < CQ; ++q) b[q] = rk(k0 + kk, lane + 32 * q);
+#pragma unroll
+                for (int r = 0; r < RW; ++r) {
+                    const float av = kk == 0 ? a[r].x : kk == 1 ? a[r].y : kk == 2 ? a[r].z : a[r].w;
+#pragma unroll
+                    for (int q = 0; q < CQ; ++q) part[r][q] += av * b[q];
+                }
+            }
+        }
+        flush();
+    };
+    auto put = [&]() {   // acc -> plane rows i0.., after every warp has read the old plane
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q)
+                if (i0 + r < ny && lane + 32 * q < nx) pl[(i0 + r) * NXP + lane + 32 * q] = acc[r][q];
+        __syncthreads();
+    };
+    const bool active = i0 < nyp;
+    // x: t1[i][j'] = sum_j rhs[i][j] Sx[j][j']
+    if (active) rows_times(pl, NXP, nx, [&](int k, int j) { return sSx[k * NXP + (j ^ (k & 31))]; });
+    put();
+    // y and the eigenvalue division: t2[i'][j'] = sum_i Sy[i][i'] t1[i][j'] / (Ly[i'] + Lx[j'] + c)
+    if (active) {
+        zero(acc);
+        zero(part);
+        for (int k = 0; k < ny; ++k) {
+            if (k > 0 && k % KB == 0) flush();
+            const float4 s0 = *reinterpret_cast<const float4 *>(sSy + k * nyp + i0);
+            const float4 s1 = *reinterpret_cast<const float4 *>(sSy + k * nyp + i0 + 4);
+            const float sv[RW] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+            float b[CQ];
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) b[q] = pl[k * NXP + lane + 32 * q];
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+#pragma unroll
+                for (int q = 0; q < CQ; ++q) part[r][q] += sv[r] * b[q];
+        }
+        flush();
+        const float c = cpl[p % cpl_mod];
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int i = i0 + r, j = lane + 32 * q;
+                if (i < ny && j < nx) {
+                    const float d = Ly[i] + Lx[j] + c;
+                    acc[r][q] = (d != 0.f) ? acc[r][q] / d : 0.f;
+                }
+            }
+    }
+    put();
+    // y^T: t3[i][j'] = sum_i' Sy[i][i'] t2[i'][j']
+    if (active) rows_times(sSy, nyp, ny, [&](int k, int j) { return pl[k * NXP + j]; });
+    put();
+    // x^T: out[i][j] = sum_j' t3[i][j'] Sx[j][j']
+    if (active) {
+        rows_times(pl, NXP, nx, [&](int k, int j) { return sSx[j * NXP + (k ^ (j & 31))]; });
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int i = i0 + r, j = lane + 32 * q;
+                if (i >= ny || j >= nx) continue;
+                const long long o = p * n2 + (long long)i * nx + j;
+                out[o] = acc[r][q];
+                if (C2) {
+                    float v = -Mx[j] * My[i] * acc[r][q];
+                    if (face2 && i == 0) v += face2[(long long)p * nx + j];
+                    C2[o] = v;
+                }
+            }
     }
 }
 

@@ -22,6 +22,7 @@ PF_BC_DIRICHLET, PF_BC_NEUMANN = 0, 1
 PF_FP64, PF_MIXED, PF_MIXED_SIMT = 0, 1, 2
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
 PF_MODEL_FULL, PF_MODEL_EQUILIBRIUM = 0, 1
+PF_GEMM_TC, PF_GEMM_PLANE, PF_GEMM_SIMT32, PF_GEMM_SIMT64, PF_GEMM_SIMT32X64 = 0, 1, 32, 64, 2
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64
 KERNEL_CLASSES = ["gemm", "fwd", "inv", "potential", "chem", "momentum", "ugradp", "efield", "other"]
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = True):
     L.pf_geometry.argtypes = [c_void_p, dp, dp, POINTER(c_int)]
     L.pf_profile.argtypes = [c_void_p, c_int]
     L.pf_autotune.argtypes = [c_void_p, c_int, POINTER(c_int), dp]
+    L.pf_set_variant.argtypes = [c_void_p, c_int, c_int, c_int]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
                                   POINTER(POINTER(c_double)), c_void_p, POINTER(c_void_p)]
@@ -95,6 +97,7 @@ def load(build_if_missing: bool = True):
     L.pf_batch_run_to_equilibrium.argtypes = [c_void_p, c_double, c_int, c_int, POINTER(c_int)]
     L.pf_batch_get_fields.argtypes = [c_void_p, c_int, c_uint, dp, c_size_t]
     L.pf_batch_autotune.argtypes = [c_void_p, c_int, dp]
+    L.pf_batch_set_variant.argtypes = [c_void_p, c_int, c_int]
     L.pf_batch_groups.argtypes = [c_void_p, POINTER(c_int)]
     L.pf_batch_destroy.argtypes = [c_void_p]
     L.pf_batch_destroy.restype = None
@@ -265,6 +268,10 @@ class Solver:
         _check(load().pf_autotune(self._h, int(steps), ctypes.byref(ch), _dp(ms)), self._h)
         return int(ch.value), float(ms[0])
 
+    def set_variant(self, gemm: int, fuse_y: bool = True, tile: int = 0):
+        """Pin the transform variant (a PF_GEMM_* code), the fused y pair and the z-transform tile."""
+        _check(load().pf_set_variant(self._h, int(gemm), int(bool(fuse_y)), int(tile)), self._h)
+
     def profile(self, enable: bool):
         _check(load().pf_profile(self._h, int(bool(enable))), self._h)
 
@@ -373,6 +380,11 @@ class Batch:
         g = (c_int * self.n)()
         ng = load().pf_batch_groups(self._h, g)
         return ng, np.array(list(g))
+
+    def set_variant(self, gemm: int, fuse_y: bool = True):
+        rc = load().pf_batch_set_variant(self._h, int(gemm), int(bool(fuse_y)))
+        if rc < 0:
+            _check_b(rc)
 
     def autotune(self, steps: int = 5):
         ng, _ = self.groups()

@@ -58,9 +58,13 @@ def test_fullsize_mirror_symmetry(fp64_run):
     assert scale["uz"] > 1e-10 and scale["ux"] > 1e-10          # the drop moves
 
 
-def test_fullsize_mixed_within_bars_of_fp64(fp64_run):
+@pytest.mark.parametrize("gemm", [None, native.PF_GEMM_TC, native.PF_GEMM_PLANE, native.PF_GEMM_SIMT64])
+def test_fullsize_mixed_within_bars_of_fp64(fp64_run, gemm):
+    """The mixed path (default, then each transform variant pinned) after five steps."""
     wl, _, _, f64 = fp64_run
     h = native.from_workload(wl, precision=native.PF_MIXED)
+    if gemm is not None:
+        h.set_variant(gemm)
     h.step(5)
     f32 = h.get(ALL)
     h.close()

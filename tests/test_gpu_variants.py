@@ -1,0 +1,130 @@
+"""Every transform variant of the fast-diagonalisation solves (tensor cores, whole plane in shared
+memory, SIMT tiles; y pair fused or separate; z-transform tiles) against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads
+from oracle.sem import Mesh2D
+from paper_2305_09020_gb300 import native
+
+from gpu_util import ALL, oracle_fields, rel_errors, run_pair
+
+pytestmark = pytest.mark.gpu
+
+FP32_VARIANTS = [(native.PF_GEMM_TC, 1), (native.PF_GEMM_PLANE, 1), (native.PF_GEMM_SIMT32, 0),
+                 (native.PF_GEMM_SIMT32, 1), (native.PF_GEMM_SIMT64, 1), (native.PF_GEMM_SIMT32X64, 0)]
+
+
+def _direct(m, bcset, shift, f):
+    """(K + shift M) x = M f with the Dirichlet rows of the bcset eliminated (x = 0 there)."""
+    Dn = []
+    if bcset == native.PF_BCSET_V:
+        Dn = list(m.bottom_nodes) + list(m.top_nodes)
+    elif bcset == native.PF_BCSET_U:
+        Dn = list(m.bottom_nodes)
+    free = np.setdiff1d(np.arange(m.n2), Dn)
+    lu = spla.splu(m.helmholtz(shift).tocsr()[free][:, free].tocsc())
+    out = np.zeros_like(f)
+    for pl in range(f.shape[0]):
+        out[pl, free] = lu.solve((m.Mdiag * f[pl])[free])
+    return out
+
+
+@pytest.mark.parametrize("gemm,fuse_y", FP32_VARIANTS)
+@pytest.mark.parametrize("mesh", [(5, 4, 6), (16, 8, 8)])
+@pytest.mark.parametrize("bcset", [native.PF_BCSET_V, native.PF_BCSET_U])
+def test_helmholtz_variant(gemm, fuse_y, mesh, bcset):
+    """A ragged plane (30 x 25 nodes) and the 128 x 65 plane of the 16 x 8, order-8 mesh, one
+    Fourier mode pair, each variant within the FP32 bar of the assembled direct solve."""
+    ex, ey, K = mesh
+    wl = workloads.small3d(ex=ex, ey=ey, order=K, nz=4)
+    g = native.from_workload(wl, precision=native.PF_MIXED)
+    g.set_variant(gemm, fuse_y=fuse_y)
+    m = Mesh2D(wl.mesh.xb, wl.mesh.yb, wl.mesh.order)
+    mode, lam = 1, 3.0
+    beta = 2 * np.pi * mode / wl.mesh.lz
+    f = np.random.default_rng(7 + bcset).standard_normal((2, m.n2))
+    x = g.solve_helmholtz(bcset, mode, lam, f).reshape(2, m.n2)
+    g.close()
+    ref = _direct(m, bcset, lam + beta ** 2, f)
+    for pl in range(2):
+        assert np.linalg.norm(x[pl] - ref[pl]) <= 2e-6 * np.linalg.norm(ref[pl])
+
+
+@pytest.mark.parametrize("gemm,fuse_y", FP32_VARIANTS)
+def test_step_variant_3d(gemm, fuse_y):
+    """Ten mixed-precision steps of a small 3D run with each variant pinned, against the oracle
+    (the bars of the mixed path: 5e-5 on V, phi, psi and 5e-4 on the derived fields)."""
+    from oracle.runner import solver_of
+    wl = workloads.small3d(ex=4, ey=2, order=5, nz=8)
+    ora = solver_of(wl)
+    g = native.from_workload(wl, precision=native.PF_MIXED)
+    g.set_variant(gemm, fuse_y=fuse_y, tile=8)
+    for _ in range(10):
+        ora.step()
+    g.step(10)
+    errs = rel_errors(g.get(ALL), oracle_fields(ora))
+    g.close()
+    for k, v in errs.items():
+        assert v <= (5e-5 if k in ("V", "phi", "psi") else 5e-4), (k, v)
+
+
+def test_set_variant_rejects_what_the_run_cannot_use():
+    wl = workloads.small3d(ex=2, ey=2, order=4, nz=4)
+    g64 = native.from_workload(wl, precision=native.PF_FP64)
+    gs = native.from_workload(wl, precision=native.PF_MIXED_SIMT)
+    for h, args in [(g64, (native.PF_GEMM_PLANE, True, 0)), (g64, (native.PF_GEMM_TC, True, 0)),
+                    (gs, (native.PF_GEMM_TC, True, 0)), (gs, (48, True, 0)), (gs, (native.PF_GEMM_SIMT32, True, 6))]:
+        with pytest.raises(native.PfError) as e:
+            h.set_variant(*args)
+        assert e.value.code == native.PF_EINVAL
+    gs.set_variant(native.PF_GEMM_PLANE, tile=16)    # FP32 without tensor cores can take the plane solve
+    gs.step(3)
+    g64.set_variant(native.PF_GEMM_SIMT64, fuse_y=False, tile=4)
+    g64.step(3)
+    g64.close()
+    gs.close()
+
+
+def test_batch_plane_variant_matches_oracle():
+    from oracle.runner import solver_of
+    from test_gpu_batch import uneven_runs
+    runs = uneven_runs()
+    b = native.Batch(runs, precision=native.PF_MIXED)
+    b.set_variant(native.PF_GEMM_PLANE)
+    oras = [solver_of(wl) for wl in runs]
+    for _ in range(4):
+        for o in oras:
+            o.step()
+    b.step(4)
+    for r, ora in enumerate(oras):
+        errs = rel_errors(b.get(r, ALL), oracle_fields(ora), skip=("Ez", "uz"))
+        for k, v in errs.items():
+            assert v <= (5e-5 if k in ("V", "phi", "psi") else 5e-4), (r, k, v)
+    b.close()
+    bf = native.Batch(runs, precision=native.PF_FP64)
+    with pytest.raises(native.PfError):
+        bf.set_variant(native.PF_GEMM_PLANE)
+    bf.close()
+
+
+@pytest.mark.parametrize("with_stream", [True, False])
+def test_autotune_advances_the_stated_steps_and_keeps_parity(with_stream):
+    """pf_autotune times every variant (graph replays on a stream of its own, eager launches on the
+    legacy stream), advances the run by 10 (steps + 2) steps, and the run stays on the FP64 oracle."""
+    from oracle.runner import solver_of
+    torch = pytest.importorskip("torch")
+    wl = workloads.small3d(ex=4, ey=2, order=4, nz=8)
+    s = torch.cuda.Stream() if with_stream else None
+    g = native.from_workload(wl, precision=native.PF_FP64, stream=s.cuda_stream if s is not None else None)
+    choice, ms = g.autotune(steps=1)
+    assert ms > 0 and choice % 1000 in (native.PF_GEMM_SIMT32, native.PF_GEMM_SIMT64, native.PF_GEMM_SIMT32X64)
+    assert choice // 1000 in (4, 8, 16, 32)
+    g.step(3)
+    ora = solver_of(wl)
+    for _ in range(1 + 10 * 3 + 3):
+        ora.step()
+    errs = rel_errors(g.get(ALL), oracle_fields(ora))
+    g.close()
+    assert all(v <= 1e-11 for v in errs.values()), errs
