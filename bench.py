@@ -318,7 +318,10 @@ def main():
                        "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                        "fdm_gemm": {0: "tcgen05 3xTF32", 1: "whole solve per plane in shared memory (SIMT)",
-                                    2: "SIMT 32x64 tiles"}.get(gemm_choice, f"SIMT {gemm_choice}x{gemm_choice} tiles")
+                                    2: "SIMT 32x64 tiles", 3: "SIMT 64x64 tiles, cp.async pipeline",
+                                    4: "SIMT 32x32 tiles, cp.async pipeline", 5: "SIMT 32x64 tiles, cp.async pipeline",
+                                    6: "whole solve per plane on a 4-block cluster (SIMT, distributed shared memory)",
+                                    7: "whole solve per plane on a 2-block cluster (SIMT, distributed shared memory)"}.get(gemm_choice, f"SIMT {gemm_choice}x{gemm_choice} tiles")
                                    + " (autotuned)",
                        "fft_pencils_per_block": fft_tile,
                        "parallelism": f"replicas x{world}"},

@@ -218,29 +218,43 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
  *   PF_GEMM_PLANE    the whole solve of a mode plane in one thread block, plane and eigenbases
  *                    in shared memory (FP32 precisions; n_x <= 128, n_y <= 128)
  *   PF_GEMM_SIMT32 / PF_GEMM_SIMT64 / PF_GEMM_SIMT32X64
- *                    CUDA-core transforms with 32x32, 64x64 or 32x64 output tiles
- * All give the same result up to rounding order. */
+ *                    CUDA-core transforms with 32x32, 64x64 or 32x64 output tiles, the next k
+ *                    tile prefetched through registers
+ *   PF_GEMM_PIPE64 / PF_GEMM_PIPE32 / PF_GEMM_PIPE32X64
+ *                    the same tiles with a four-stage cp.async pipeline (three k tiles in flight)
+ *   PF_GEMM_CLUSTER4 / PF_GEMM_CLUSTER2
+ *                    the whole solve of a mode plane on a cluster of 4 / 2 thread blocks that
+ *                    exchange the plane through distributed shared memory (FP32 precisions;
+ *                    n_x <= 128, n_y <= 128)
+ * All give the same result up to rounding order; in FP64 the CUDA-core variants sum in the same
+ * order and agree bit for bit. */
 #define PF_GEMM_TC 0
 #define PF_GEMM_PLANE 1
 #define PF_GEMM_SIMT32 32
 #define PF_GEMM_SIMT64 64
 #define PF_GEMM_SIMT32X64 2
+#define PF_GEMM_PIPE64 3
+#define PF_GEMM_PIPE32 4
+#define PF_GEMM_PIPE32X64 5
+#define PF_GEMM_CLUSTER4 6
+#define PF_GEMM_CLUSTER2 7
 
 /* Autotuner of a single run: time `steps` steady steps with each transform variant available to
- * the run (PF_GEMM_*), keep the fastest, then (unless PF_GEMM_PLANE won) whether the y transforms
+ * the run (PF_GEMM_*), keep the fastest, then (unless a whole-plane variant won) whether the y transforms
  * run fused (one pass, eigenbasis in shared memory), then (3D) the z-transform tile of 4, 8, 16
  * or 32 pencils per block.  Each candidate is timed as the run executes its steady steps: graph
  * replays when the run has its own stream, eager launches on the legacy stream.  The run advances
- * by 10 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile with gemm a PF_GEMM_*
+ * by 15 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile with gemm a PF_GEMM_*
  * code and tile = 0 in 2D; ms_per_step (nullable) the best time. */
 int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);
 
 /* Pin the transform variant without timing (to reproduce an autotuned choice or to compare
  * variants): gemm a PF_GEMM_* code, fuse_y 1 to run the y transform pair fused where it fits
- * (0 separately; ignored by PF_GEMM_PLANE), tile the pencils per z-transform block (4, 8, 16,
+ * (0 separately; ignored by the whole-plane variants), tile the pencils per z-transform block (4, 8, 16,
  * 32) or 0 for the size heuristic.  Synchronises the run's stream and drops its captured
  * graphs.  PF_EINVAL (nothing changed) when a value is outside these sets or the run cannot use
- * the variant (PF_GEMM_TC outside PF_MIXED, PF_GEMM_PLANE in FP64 or on a plane too large). */
+ * the variant (PF_GEMM_TC outside PF_MIXED, the whole-plane variants in FP64 or on a plane too
+ * large). */
 int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile);
 
 /* Geometry queries: nodes_x[n_x], nodes_y[n_y] (either may be NULL), sizes in dims[4]
@@ -281,15 +295,19 @@ int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_steps, int chec
 int pf_batch_get_fields(pf_batch *b, int run, unsigned mask, double *host_out, size_t n);
 
 /* Autotuner: for every group, time `steps` steps with each transform variant (tensor cores
- * where the precision has them, SIMT with 32x32 and 64x64 tiles, the whole-plane solve where it
- * fits) and keep the fastest.  It advances the ensemble by 4 (steps + 1) steps (rounded up to
- * even).  ms_out[g] (nullable, capacity >= number of groups) receives the best time per step of
+ * where the precision has them, SIMT with 32x32 and 64x64 tiles, the whole-plane solves on one
+ * block or a cluster where they fit) and keep the fastest.  It advances the ensemble by
+ * 6 (steps + 1) steps (rounded up to even).  ms_out[g] (nullable, capacity >= number of groups) receives the best time per step of
  * group g; returns the number of groups (>= 0) or an error code. */
 int pf_batch_autotune(pf_batch *b, int steps, double *ms_out);
 
 /* Pin the transform variant of every group (codes as pf_set_variant); PF_EINVAL, nothing
  * changed, when some group cannot use it. */
 int pf_batch_set_variant(pf_batch *b, int gemm, int fuse_y);
+
+/* Message of the ensemble's last failed call (empty if none; pf_last_error(NULL)'s message for
+ * b == NULL).  The string is owned by the ensemble and valid until its next call. */
+const char *pf_batch_last_error(const pf_batch *b);
 
 /* Number of groups and, per run, its group (group_of[nrun], nullable). */
 int pf_batch_groups(const pf_batch *b, int *group_of);

@@ -37,8 +37,21 @@ struct CudaError {
 #define PF_CU(call)                                                                  \
     do {                                                                             \
         cudaError_t e_ = (call);                                                     \
-        if (e_ != cudaSuccess) throw CudaError{e_, std::string(#call)};              \
+        if (e_ != cudaSuccess) {                                                     \
+            cudaGetLastError(); /* a non-sticky error must not resurface later */    \
+            throw CudaError{e_, std::string(#call)};                                 \
+        }                                                                            \
     } while (0)
+
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The limit belongs to the function,
+// not to an engine: lowering it for a small mesh would make a larger engine's launches invalid.
+void raise_smem_limit(const void *fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    cudaFuncAttributes fa{};
+    PF_CU(cudaFuncGetAttributes(&fa, fn));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < bytes)
+        PF_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
 
 struct HostSetup {
     int ex, ey, K, p, nx, ny, nz;
@@ -328,14 +341,24 @@ struct Engine {
         RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
         if (fdm_y_smem() > 48 * 1024 && fdm_y_smem() <= 200 * 1024)
-            PF_CU(cudaFuncSetAttribute(pf::k_fdm_y<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fdm_y_smem()));
+            raise_smem_limit((const void *)pf::k_fdm_y<T, 32, 8>, fdm_y_smem());
         if constexpr (sizeof(T) == 4) {
             if (plane_fits()) {   // opt in once, before any graph capture
                 const int cq = plane_cq();
                 const void *fn = cq == 1 ? (const void *)pf::k_fdm_plane<1>
                                  : cq == 2 ? (const void *)pf::k_fdm_plane<2> : (const void *)pf::k_fdm_plane<4>;
-                PF_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fdm_plane_smem()));
+                raise_smem_limit(fn, fdm_plane_smem());
+            }
+            const int cq = plane_cq();
+            if (cluster_fits(4)) {
+                const void *fn = cq == 1 ? (const void *)pf::k_fdm_cluster<4, 1>
+                                 : cq == 2 ? (const void *)pf::k_fdm_cluster<4, 2> : (const void *)pf::k_fdm_cluster<4, 4>;
+                raise_smem_limit(fn, fdm_cluster_smem(4));
+            }
+            if (cluster_fits(2)) {
+                const void *fn = cq == 1 ? (const void *)pf::k_fdm_cluster<2, 1>
+                                 : cq == 2 ? (const void *)pf::k_fdm_cluster<2, 2> : (const void *)pf::k_fdm_cluster<2, 4>;
+                raise_smem_limit(fn, fdm_cluster_smem(2));
             }
         }
 
@@ -356,7 +379,7 @@ struct Engine {
                 add_tc(Sy[b], tr(s.Sy[b], ny), ny);
                 add_tc(SyT[b], s.Sy[b], ny);
             }
-            PF_CU(cudaFuncSetAttribute(pf::k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(16)));
+            raise_smem_limit((const void *)pf::k_gemm_tc<16>, tc_smem(16));
         }
         PF_CU(cudaStreamSynchronize(st));
     }
@@ -481,6 +504,27 @@ struct Engine {
         }
         pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod, C2, Mx, My, face2};
         constexpr int BK = sizeof(T) == 8 ? 8 : 16;
+        if (simt_tile >= 3 && simt_tile <= 5) {   // cp.async pipelines: 64x64, 32x32, 32x64 tiles
+            constexpr int VWE = 16 / (int)sizeof(T);
+            const bool vec = Ncol % VWE == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0;
+            prof->begin(PF_KC_GEMM, st);
+            if (simt_tile == 3) {
+                dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 63) / 64));
+                if (vec) pf::k_gemm_cp<T, 64, 64, BK, 4, 4, 4, true><<<grid, 256, 0, st>>>(g);
+                else pf::k_gemm_cp<T, 64, 64, BK, 4, 4, 4, false><<<grid, 256, 0, st>>>(g);
+            } else if (simt_tile == 4) {
+                dim3 grid((Ncol + 31) / 32, (unsigned)((Mrows + 31) / 32));
+                if (vec) pf::k_gemm_cp<T, 32, 32, BK, 2, 4, 4, true><<<grid, 128, 0, st>>>(g);
+                else pf::k_gemm_cp<T, 32, 32, BK, 2, 4, 4, false><<<grid, 128, 0, st>>>(g);
+            } else {
+                dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 31) / 32));
+                if (vec) pf::k_gemm_cp<T, 32, 64, BK, 2, 4, 4, true><<<grid, 256, 0, st>>>(g);
+                else pf::k_gemm_cp<T, 32, 64, BK, 2, 4, 4, false><<<grid, 256, 0, st>>>(g);
+            }
+            check_launch();
+            prof->end(st);
+            return;
+        }
         const long long tiles64 = ((Ncol + 63) / 64) * ((Mrows + 63) / 64);
         prof->begin(PF_KC_GEMM, st);
         const bool big = simt_tile == 64 || (simt_tile == 0 && tiles64 >= 4 * 152 && Ncol % 64 > 32);
@@ -513,6 +557,53 @@ struct Engine {
         return sizeof(T) == 4 && nx <= 128 && ny <= 128 && fdm_plane_smem() <= 227 * 1024;
     }
     bool fuse_plane = false;   // chosen by the autotuner when it is faster
+    // the cluster solve (FP32): CL blocks per plane; shared memory per block
+    int cluster = 0;
+    size_t fdm_cluster_smem(int CL) const {
+        const size_t nxp = 32 * plane_cq(), rc = (ny + CL - 1) / CL, xc = (nx + CL - 1) / CL;
+        return (nxp * nxp + (size_t)ny * ny + rc * nxp + (size_t)ny * xc) * sizeof(float);
+    }
+    bool cluster_fits(int CL) const {
+        return sizeof(T) == 4 && (CL == 2 || CL == 4) && nx <= 128 && ny <= 128 && nx >= CL && ny >= CL &&
+               fdm_cluster_smem(CL) <= 227 * 1024;
+    }
+    template <int CL, int CQ>
+    void launch_cluster(const T *rhs, T *out, int bcset, const T *sh, long long P, T *c2, const T *face) {
+        if constexpr (sizeof(T) == 4) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(P * CL));
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = fdm_cluster_smem(CL);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = CL;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            PF_CU(cudaLaunchKernelEx(&cfg, pf::k_fdm_cluster<CL, CQ>, rhs, out, nx, ny, Sx, Sy[bcset], Lx, Ly[bcset],
+                                     sh, nz, c2, Mx, My, face));
+        }
+    }
+    template <int CL>
+    void cluster_cq(const T *rhs, T *out, int bcset, const T *sh, long long P, T *c2, const T *face) {
+        const int cq = plane_cq();
+        if (cq == 1) launch_cluster<CL, 1>(rhs, out, bcset, sh, P, c2, face);
+        else if (cq == 2) launch_cluster<CL, 2>(rhs, out, bcset, sh, P, c2, face);
+        else launch_cluster<CL, 4>(rhs, out, bcset, sh, P, c2, face);
+    }
+    // transform variant by its public code (PF_GEMM_*); false when this engine cannot run it
+    bool gemm_available(int code) const {
+        return (code == 0 && !tcb.empty()) || (code == 1 && plane_fits()) || code == 32 || code == 64 ||
+               (code >= 2 && code <= 5) || (code == 6 && cluster_fits(4)) || (code == 7 && cluster_fits(2));
+    }
+    void set_gemm(int code) {
+        use_tc = code == 0;
+        fuse_plane = code == 1;
+        cluster = code == 6 ? 4 : code == 7 ? 2 : 0;
+        simt_tile = (code == 32 || code == 64 || (code >= 2 && code <= 5)) ? code : 0;
+    }
     template <int CQ>
     void launch_plane(const T *rhs, T *out, int bcset, const T *sh, long long P, T *c2, const T *face) {
         if constexpr (sizeof(T) == 4) {
@@ -525,6 +616,14 @@ struct Engine {
     void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
              const T *face = nullptr) {
         const long long P = nplanes;
+        if (cluster && cluster_fits(cluster)) {
+            prof->begin(PF_KC_GEMM, st);
+            if (cluster == 4) cluster_cq<4>(rhs, out, bcset, sh, P, minus_m_out, face);
+            else cluster_cq<2>(rhs, out, bcset, sh, P, minus_m_out, face);
+            check_launch();
+            prof->end(st);
+            return;
+        }
         if (fuse_plane && plane_fits()) {
             prof->begin(PF_KC_GEMM, st);
             const int cq = plane_cq();
@@ -1303,28 +1402,21 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
         PF_CU(cudaEventElapsedTime(&ms, e0, e1));
         return (double)ms / steps;
     };
-    struct Cand { bool tc; int tile; };
-    std::vector<Cand> cands;
-    if (!E.tcb.empty()) cands.push_back({true, 0});
-    cands.push_back({false, 32});
-    cands.push_back({false, 64});
-    cands.push_back({false, 2});
-    if (E.plane_fits()) cands.push_back({false, -1});   // whole solve per plane in shared memory
-    Cand pick = cands[0];
+    // every variant this engine can run (PF_GEMM_* codes)
+    std::vector<int> cands;
+    for (int code : {0, 32, 64, 2, 3, 4, 5, 1, 6, 7})
+        if (E.gemm_available(code)) cands.push_back(code);
+    int pick = cands[0];
     double best = INFINITY;
     int taken = 0;
-    for (const Cand &c : cands) {
-        E.use_tc = c.tc;
-        E.simt_tile = c.tile < 0 ? 0 : c.tile;
-        E.fuse_plane = c.tile < 0;
+    for (int code : cands) {
+        E.set_gemm(code);
         const double ms = time_variant(taken);
-        if (ms < best) { best = ms; pick = c; }
+        if (ms < best) { best = ms; pick = code; }
     }
-    E.use_tc = pick.tc;
-    E.simt_tile = pick.tile < 0 ? 0 : pick.tile;
-    E.fuse_plane = pick.tile < 0;
-    // the fused y pair against the two separate y transforms
-    if (!E.fuse_plane) {
+    E.set_gemm(pick);
+    // the fused y pair against the two separate y transforms (the whole-plane solves have no y pair)
+    if (!E.fuse_plane && !E.cluster) {
         E.fuse_y = !E.fuse_y;
         const double ms = time_variant(taken);
         if (ms < best) best = ms;
@@ -1342,7 +1434,7 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
     }
     drop_graphs();
     for (; taken < total; ++taken) E.step(2);
-    if (choice) *choice = (pick.tc ? 0 : (pick.tile < 0 ? 1 : pick.tile)) + 1000 * E.tp_override;
+    if (choice) *choice = pick + 1000 * E.tp_override;
     if (best_ms) *best_ms = best;
 }
 }  // namespace
@@ -1351,7 +1443,7 @@ extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_
     if (!h || steps < 1) return PF_EINVAL;
     try {
         if (h->nstep < 1) pf_step(h, 1);
-        int total = 10 * (steps + 2);   // at most 5 GEMM variants + the y pair + 4 tiles
+        int total = 15 * (steps + 2);   // at most 10 GEMM variants + the y pair + 4 tiles
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));
         PF_CU(cudaEventCreate(&e1));
@@ -1372,13 +1464,9 @@ namespace {
 // pin the transform variants of one engine; false when the engine cannot use them
 template <typename T>
 bool set_variant(Engine<T> &E, int gemm, int fuse_y, int tile) {
-    const bool gemm_ok = (gemm == 0 && !E.tcb.empty()) || (gemm == 1 && E.plane_fits()) || gemm == 32 ||
-                         gemm == 64 || gemm == 2;
     const bool tile_ok = tile == 0 || tile == 4 || tile == 8 || tile == 16 || tile == 32;
-    if (!gemm_ok || (fuse_y != 0 && fuse_y != 1) || !tile_ok) return false;
-    E.use_tc = gemm == 0;
-    E.fuse_plane = gemm == 1;
-    E.simt_tile = gemm >= 2 ? gemm : 0;
+    if (!E.gemm_available(gemm) || (fuse_y != 0 && fuse_y != 1) || !tile_ok) return false;
+    E.set_gemm(gemm);
     E.fuse_y = fuse_y == 1;
     E.tp_override = tile;
     for (int c = 0; c < 2; ++c)
@@ -1700,6 +1788,11 @@ extern "C" int pf_batch_get_fields(pf_batch *b, int run, unsigned mask, double *
     return PF_OK;
 }
 
+extern "C" const char *pf_batch_last_error(const pf_batch *b) {
+    if (!b) return g_create_error.c_str();
+    return b->err.c_str();
+}
+
 extern "C" int pf_batch_set_variant(pf_batch *b, int gemm, int fuse_y) {
     if (!b) return PF_EINVAL;
     try {
@@ -1707,8 +1800,7 @@ extern "C" int pf_batch_set_variant(pf_batch *b, int gemm, int fuse_y) {
         for (auto &gp : b->groups) {   // every group must be able to take the variant
             bool ok = true;
             for_engine(*gp, [&](auto &E) {
-                ok = (gemm == 0 && !E.tcb.empty()) || (gemm == 1 && E.plane_fits()) || gemm == 32 || gemm == 64 ||
-                     gemm == 2;
+                ok = E.gemm_available(gemm);
             });
             if (!ok || (fuse_y != 0 && fuse_y != 1))
                 return batch_fail(b, PF_EINVAL, "pf_batch_set_variant: variant not available for every group");
@@ -1729,26 +1821,21 @@ extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));
         PF_CU(cudaEventCreate(&e1));
-        // every group takes the same number of steps (4 variants x (steps + 1), rounded up to an
+        // every group takes the same number of steps (6 variants x (steps + 1), rounded up to an
         // even count so the history-slot parity of all groups stays equal)
-        int total = 4 * (steps + 1);
+        int total = 6 * (steps + 1);
         if (total % 2) total += 1;
         for (size_t gi = 0; gi < b->groups.size(); ++gi) {
             auto &g = *b->groups[gi];
             double best = INFINITY;
             for_engine(g, [&](auto &E) {
-                struct Cand { bool tc; int tile; };
-                std::vector<Cand> cands;
-                if (!E.tcb.empty()) cands.push_back({true, 0});
-                cands.push_back({false, 32});
-                cands.push_back({false, 64});
-                if (E.plane_fits()) cands.push_back({false, -1});
-                Cand pick = cands[0];
+                std::vector<int> cands;
+                for (int code : {0, 32, 64, 1, 6, 7})
+                    if (E.gemm_available(code)) cands.push_back(code);
+                int pick = cands[0];
                 int taken = 0;
-                for (const Cand &c : cands) {
-                    E.use_tc = c.tc;
-                    E.simt_tile = c.tile < 0 ? 0 : c.tile;
-                    E.fuse_plane = c.tile < 0;
+                for (int code : cands) {
+                    E.set_gemm(code);
                     E.step(2);   // warm-up of this variant
                     PF_CU(cudaEventRecord(e0, E.st));
                     for (int s = 0; s < steps; ++s) E.step(2);
@@ -1757,11 +1844,9 @@ extern "C" int pf_batch_autotune(pf_batch *b, int steps, double *ms_out) {
                     taken += steps + 1;
                     float ms = 0.f;
                     PF_CU(cudaEventElapsedTime(&ms, e0, e1));
-                    if (ms / steps < best) { best = ms / steps; pick = c; }
+                    if (ms / steps < best) { best = ms / steps; pick = code; }
                 }
-                E.use_tc = pick.tc;
-                E.simt_tile = pick.tile < 0 ? 0 : pick.tile;
-                E.fuse_plane = pick.tile < 0;
+                E.set_gemm(pick);
                 for (; taken < total; ++taken) E.step(2);
             });
             if (ms_out) ms_out[gi] = best;

@@ -26,6 +26,7 @@
 //   reductions   FP64 phase mass, max |u|, max |difference|
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1045,6 +1046,134 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
     }
 }
 
+// ---- the same transform GEMM with a cp.async multi-stage pipeline -----------------------------
+// C = A B with the epilogues of k_gemm.  STAGES - 1 k tiles are in flight (global -> shared memory
+// copies issued asynchronously), so the loop does not wait on the L2 latency of each tile.  A is
+// kept row-major in shared memory ([m][k], rows padded to BK + PAD), B as [k][n]; VEC selects
+// 16-byte copies (N a multiple of 16 / sizeof(T) and 16-byte aligned pointers), else one copy per
+// element.  Out-of-range elements are zero-filled by the copy (source size 0).
+__device__ __forceinline__ void cp_async_elem(void *sdst, const void *gsrc, int bytes, bool in) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    const int n = in ? bytes : 0;
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, int STAGES, bool VEC>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_cp(GemmArgs<T> g) {
+    constexpr int NTH = (BM / TM) * (BN / TN);
+    constexpr int VW = VEC ? 16 / (int)sizeof(T) : 1;   // elements per copy
+    constexpr int PA = 16 / (int)sizeof(T);             // A row padding (keeps rows 16-byte aligned)
+    constexpr int LDA = BK + PA;
+    constexpr int CA = BM * BK / VW, CB = BK * BN / VW;  // copies per tile
+    static_assert(TN * sizeof(T) % 16 == 0, "B fragment is read as 16-byte vectors");
+    __shared__ __align__(16) T sA[STAGES][BM][LDA];
+    __shared__ __align__(16) T sB[STAGES][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const long long m0 = (long long)blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
+    const int KT = (g.N + BK - 1) / BK;
+    auto load = [&](int slot, int kt) {
+        const int k0 = kt * BK;
+#pragma unroll
+        for (int i = 0; i < (CA + NTH - 1) / NTH; ++i) {
+            const int c = tid + NTH * i, r = c / (BK / VW), kc = (c % (BK / VW)) * VW;
+            if (CA % NTH != 0 && c >= CA) break;
+            const long long m = m0 + r;
+            const bool in = m < g.Mrows && k0 + kc < g.N;
+            cp_async_elem(&sA[slot][r][kc], in ? (const void *)(g.A + m * g.N + k0 + kc) : (const void *)g.A,
+                          VW * (int)sizeof(T), in);
+        }
+#pragma unroll
+        for (int i = 0; i < (CB + NTH - 1) / NTH; ++i) {
+            const int c = tid + NTH * i, r = c / (BN / VW), nc = (c % (BN / VW)) * VW;
+            if (CB % NTH != 0 && c >= CB) break;
+            const bool in = k0 + r < g.N && n0 + nc < g.N;
+            cp_async_elem(&sB[slot][r][nc], in ? (const void *)(g.B + (long long)(k0 + r) * g.N + n0 + nc)
+                                               : (const void *)g.B,
+                          VW * (int)sizeof(T), in);
+        }
+    };
+    // blocked summation as in k_gemm: FP32 sums each k tile separately, FP64 in one block
+    T acc[TM][TN], part[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = part[i][j] = 0;
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < KT) load(s, s);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();                       // tile kt landed for every thread; slot kt-1 is free
+        const int nk = kt + STAGES - 1;
+        if (nk < KT) load(nk % STAGES, nk);
+        cp_async_commit();
+        const int slot = kt % STAGES;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T ra[TM], rb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) ra[i] = sA[slot][ty * TM + i][kk];
+#pragma unroll
+            for (int j = 0; j < TN; j += 16 / (int)sizeof(T)) {
+                const float4 v = *reinterpret_cast<const float4 *>(&sB[slot][kk][tx * TN + j]);
+                const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                for (int q = 0; q < 16 / (int)sizeof(T); ++q) rb[j + q] = pv[q];
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) part[i][j] += ra[i] * rb[j];
+        }
+        if (sizeof(T) == 4 || kt == KT - 1) {
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    acc[i][j] += part[i][j];
+                    part[i][j] = 0;
+                }
+        }
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const long long m = m0 + ty * TM + i;
+        if (m >= g.Mrows) continue;
+        const long long p = m / g.R;
+        const int r = (int)(m - p * g.R);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx * TN + j;
+            if (n >= g.N) continue;
+            T v = acc[i][j];
+            if (g.lamN) {
+                const T d = g.lamN[n] + g.lamR[r] + g.cpl[p % g.cpl_mod];
+                v = (d != T(0)) ? v / d : T(0);
+            }
+            if (g.store == 0) g.C[m * g.N + n] = v;
+            else g.C[(p * g.N + n) * g.R + r] = v;
+            if (g.C2) {
+                T w = -g.m2x[n] * g.m2y[r] * v;
+                if (g.face2 && r == 0) w += g.face2[p * g.N + n];
+                g.C2[m * g.N + n] = w;
+            }
+        }
+    }
+}
+
 // dst(t, src(t)) for t < n by the whole block, U independent global loads in flight per thread
 // before their shared-memory stores (a plain strided loop waits on each load in turn)
 template <int U, typename T, typename Src, typename Dst>
@@ -1294,6 +1423,208 @@ __global__ void __launch_bounds__(512) k_fdm_plane(const float *__restrict__ rhs
                     float v = -Mx[j] * My[i] * acc[r][q];
                     if (face2 && i == 0) v += face2[(long long)p * nx + j];
                     C2[o] = v;
+                }
+            }
+    }
+}
+
+// ---- a fast-diagonalisation solve per mode plane on a cluster of CL thread blocks ----------------
+// out[p] = Sy [ (Sy^T rhs[p] Sx) / (Ly + Lx + c_p) ] Sx^T (FP32) with the optional second output of
+// k_gemm.  The cluster of plane p = blockIdx.x / CL splits the plane: block r owns the rows
+// [r RC, (r+1) RC) for the two x transforms and the columns [r XC, (r+1) XC) for the two y
+// transforms (RC = ceil(ny / CL), XC = ceil(nx / CL)).  After the x transform every block writes
+// its rows' pieces into the owners' column buffers (distributed shared memory), after the y^T
+// transform the pieces go back into the owners' row buffers; two cluster barriers order these
+// exchanges.  Shared memory (floats): Sx NXP^2 (columns XOR-swizzled by the row, as in
+// k_fdm_plane), Sy ny^2, row buffer RC x NXP, column buffer ny x XC.  Each k sum is blocked by 16.
+// Every thread passes the same three cluster barriers and two block barriers (no early exit).
+template <int CL, int CQ>
+__global__ void __launch_bounds__(256) k_fdm_cluster(const float *__restrict__ rhs, float *__restrict__ out, int nx,
+                                                      int ny, const float *__restrict__ Sx,
+                                                      const float *__restrict__ Sy, const float *__restrict__ Lx,
+                                                      const float *__restrict__ Ly, const float *__restrict__ cpl,
+                                                      int cpl_mod, float *__restrict__ C2,
+                                                      const float *__restrict__ Mx, const float *__restrict__ My,
+                                                      const float *__restrict__ face2) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    constexpr int NXP = 32 * CQ, NW = 8, KB = 16;
+    constexpr int RTX = 64 / NW;                 // x stages: up to 64 rows per block
+    constexpr int RTY = 128 / NW;                // y stages: up to 128 rows (ny)
+    constexpr int CQY = CL >= 4 ? 1 : 2;         // y stages: up to 32 CQY columns per block
+    extern __shared__ __align__(16) unsigned char pf_smem_raw[];
+    const int rank = (int)cl.block_rank();
+    const int p = blockIdx.x / CL;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int RC = (ny + CL - 1) / CL, XC = (nx + CL - 1) / CL;
+    const int row0 = rank * RC, nrow = max(0, min(RC, ny - row0));
+    const int col0 = rank * XC, ncol = max(0, min(XC, nx - col0));
+    const long long n2 = (long long)nx * ny;
+    float *sSx = reinterpret_cast<float *>(pf_smem_raw);
+    float *sSy = sSx + NXP * NXP;
+    float *rowb = sSy + ny * ny;
+    float *colb = rowb + RC * NXP;
+    block_stage<8, float>(
+        NXP * NXP, [&](int t) { const int r = t / NXP, c = t % NXP; return (r < nx && c < nx) ? Sx[r * nx + c] : 0.f; },
+        [&](int t, float v) { const int r = t / NXP, c = t % NXP; sSx[r * NXP + (c ^ (r & 31))] = v; });
+    block_stage<8, float>(ny * ny, [&](int t) { return Sy[t]; }, [&](int t, float v) { sSy[t] = v; });
+    block_stage<8, float>(
+        RC * NXP,
+        [&](int t) {
+            const int r = t / NXP, c = t % NXP;
+            return (r < nrow && c < nx) ? rhs[p * n2 + (long long)(row0 + r) * nx + c] : 0.f;
+        },
+        [&](int t, float v) { rowb[t] = v; });
+    cl.sync();   // every block of the cluster is running and has its operands
+
+    // x: T1[i][j'] = sum_j rhs[i][j] Sx[j][j'] for my rows; pieces to the column owners
+    {
+        float acc[RTX][CQ], part[RTX][CQ];
+#pragma unroll
+        for (int t = 0; t < RTX; ++t)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) acc[t][q] = part[t][q] = 0.f;
+        for (int k = 0; k < nx; ++k) {
+            if (k > 0 && k % KB == 0) {
+#pragma unroll
+                for (int t = 0; t < RTX; ++t)
+#pragma unroll
+                    for (int q = 0; q < CQ; ++q) { acc[t][q] += part[t][q]; part[t][q] = 0.f; }
+            }
+            float b[CQ];
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int j = lane + 32 * q;
+                b[q] = sSx[k * NXP + (j ^ (k & 31))];
+            }
+#pragma unroll
+            for (int t = 0; t < RTX; ++t) {
+                const int i = w + NW * t;
+                if (i < nrow) {
+                    const float a = rowb[i * NXP + k];
+#pragma unroll
+                    for (int q = 0; q < CQ; ++q) part[t][q] += a * b[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RTX; ++t)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int i = w + NW * t, j = lane + 32 * q;
+                if (i < nrow && j < nx) {
+                    const int s = j / XC;
+                    cl.map_shared_rank(colb, s)[(row0 + i) * XC + (j - s * XC)] = acc[t][q] + part[t][q];
+                }
+            }
+    }
+    cl.sync();   // column buffers complete
+
+    // y and the eigenvalue division: T2[i'][j'] = sum_i Sy[i][i'] T1[i][j'] / (Ly[i'] + Lx[j'] + c),
+    // then y^T: T3[i][j'] = sum_i' Sy[i][i'] T2[i'][j'], for my columns
+    const float c = cpl[p % cpl_mod];
+    for (int pass = 0; pass < 2; ++pass) {
+        float acc[RTY][CQY], part[RTY][CQY];
+#pragma unroll
+        for (int t = 0; t < RTY; ++t)
+#pragma unroll
+            for (int q = 0; q < CQY; ++q) acc[t][q] = part[t][q] = 0.f;
+        for (int k = 0; k < ny; ++k) {
+            if (k > 0 && k % KB == 0) {
+#pragma unroll
+                for (int t = 0; t < RTY; ++t)
+#pragma unroll
+                    for (int q = 0; q < CQY; ++q) { acc[t][q] += part[t][q]; part[t][q] = 0.f; }
+            }
+            float b[CQY];
+#pragma unroll
+            for (int q = 0; q < CQY; ++q) {
+                const int j = lane + 32 * q;
+                b[q] = j < XC ? colb[k * XC + j] : 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < RTY; ++t) {
+                const int i = w + NW * t;
+                if (i < ny) {
+                    const float a = pass == 0 ? sSy[k * ny + i] : sSy[i * ny + k];
+#pragma unroll
+                    for (int q = 0; q < CQY; ++q) part[t][q] += a * b[q];
+                }
+            }
+        }
+        if (pass == 0) {
+            __syncthreads();   // every thread has read the column buffer
+#pragma unroll
+            for (int t = 0; t < RTY; ++t)
+#pragma unroll
+                for (int q = 0; q < CQY; ++q) {
+                    const int i = w + NW * t, j = lane + 32 * q;
+                    if (i < ny && j < ncol) {
+                        const float d = Ly[i] + Lx[col0 + j] + c;
+                        const float v = acc[t][q] + part[t][q];
+                        colb[i * XC + j] = (d != 0.f) ? v / d : 0.f;
+                    }
+                }
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int t = 0; t < RTY; ++t)
+#pragma unroll
+                for (int q = 0; q < CQY; ++q) {
+                    const int i = w + NW * t, j = lane + 32 * q;
+                    if (i < ny && j < ncol) {
+                        const int r = i / RC;
+                        cl.map_shared_rank(rowb, r)[(i - r * RC) * NXP + col0 + j] = acc[t][q] + part[t][q];
+                    }
+                }
+        }
+    }
+    cl.sync();   // row buffers complete; no shared memory of another block is touched after this
+
+    // x^T: out[i][j] = sum_j' T3[i][j'] Sx[j][j'] for my rows
+    {
+        float acc[RTX][CQ], part[RTX][CQ];
+#pragma unroll
+        for (int t = 0; t < RTX; ++t)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) acc[t][q] = part[t][q] = 0.f;
+        for (int k = 0; k < nx; ++k) {
+            if (k > 0 && k % KB == 0) {
+#pragma unroll
+                for (int t = 0; t < RTX; ++t)
+#pragma unroll
+                    for (int q = 0; q < CQ; ++q) { acc[t][q] += part[t][q]; part[t][q] = 0.f; }
+            }
+            float b[CQ];
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int j = lane + 32 * q;
+                b[q] = sSx[j * NXP + (k ^ (j & 31))];
+            }
+#pragma unroll
+            for (int t = 0; t < RTX; ++t) {
+                const int i = w + NW * t;
+                if (i < nrow) {
+                    const float a = rowb[i * NXP + k];
+#pragma unroll
+                    for (int q = 0; q < CQ; ++q) part[t][q] += a * b[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RTX; ++t)
+#pragma unroll
+            for (int q = 0; q < CQ; ++q) {
+                const int i = w + NW * t, j = lane + 32 * q;
+                if (i >= nrow || j >= nx) continue;
+                const int y = row0 + i;
+                const long long o = p * n2 + (long long)y * nx + j;
+                const float v = acc[t][q] + part[t][q];
+                out[o] = v;
+                if (C2) {
+                    float u = -Mx[j] * My[y] * v;
+                    if (face2 && y == 0) u += face2[(long long)p * nx + j];
+                    C2[o] = u;
                 }
             }
     }

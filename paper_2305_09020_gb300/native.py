@@ -23,6 +23,8 @@ PF_FP64, PF_MIXED, PF_MIXED_SIMT = 0, 1, 2
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
 PF_MODEL_FULL, PF_MODEL_EQUILIBRIUM = 0, 1
 PF_GEMM_TC, PF_GEMM_PLANE, PF_GEMM_SIMT32, PF_GEMM_SIMT64, PF_GEMM_SIMT32X64 = 0, 1, 32, 64, 2
+PF_GEMM_PIPE64, PF_GEMM_PIPE32, PF_GEMM_PIPE32X64 = 3, 4, 5
+PF_GEMM_CLUSTER4, PF_GEMM_CLUSTER2 = 6, 7
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64
 KERNEL_CLASSES = ["gemm", "fwd", "inv", "potential", "chem", "momentum", "ugradp", "efield", "other"]
@@ -98,6 +100,8 @@ def load(build_if_missing: bool = True):
     L.pf_batch_get_fields.argtypes = [c_void_p, c_int, c_uint, dp, c_size_t]
     L.pf_batch_autotune.argtypes = [c_void_p, c_int, dp]
     L.pf_batch_set_variant.argtypes = [c_void_p, c_int, c_int]
+    L.pf_batch_last_error.argtypes = [c_void_p]
+    L.pf_batch_last_error.restype = c_char_p
     L.pf_batch_groups.argtypes = [c_void_p, POINTER(c_int)]
     L.pf_batch_destroy.argtypes = [c_void_p]
     L.pf_batch_destroy.restype = None
@@ -357,23 +361,23 @@ class Batch:
         self._h = h
 
     def step(self, n: int = 1):
-        _check_b(load().pf_batch_step(self._h, int(n)))
+        _check_b(load().pf_batch_step(self._h, int(n)), self._h)
 
     def umax(self):
         u, m = np.zeros(self.n), np.zeros(self.n)
-        _check_b(load().pf_batch_umax(self._h, _dp(u), _dp(m)))
+        _check_b(load().pf_batch_umax(self._h, _dp(u), _dp(m)), self._h)
         return u, m
 
     def run_to_equilibrium(self, tol: float, max_steps: int, check_every: int = 100):
         out = (c_int * self.n)()
-        _check_b(load().pf_batch_run_to_equilibrium(self._h, float(tol), int(max_steps), int(check_every), out))
+        _check_b(load().pf_batch_run_to_equilibrium(self._h, float(tol), int(max_steps), int(check_every), out), self._h)
         return np.array(list(out))
 
     def get(self, run: int, mask: int) -> dict:
         ny, nx = self.shapes[run]
         names = [nm for bit, nms in _BLOCKS if mask & bit for nm in nms]
         out = np.zeros(len(names) * nx * ny)
-        _check_b(load().pf_batch_get_fields(self._h, int(run), int(mask), _dp(out), out.size))
+        _check_b(load().pf_batch_get_fields(self._h, int(run), int(mask), _dp(out), out.size), self._h)
         return {nm: out[i * nx * ny:(i + 1) * nx * ny].reshape(1, ny, nx) for i, nm in enumerate(names)}
 
     def groups(self):
@@ -384,14 +388,14 @@ class Batch:
     def set_variant(self, gemm: int, fuse_y: bool = True):
         rc = load().pf_batch_set_variant(self._h, int(gemm), int(bool(fuse_y)))
         if rc < 0:
-            _check_b(rc)
+            _check_b(rc, self._h)
 
     def autotune(self, steps: int = 5):
         ng, _ = self.groups()
         ms = np.zeros(max(1, ng))
         rc = load().pf_batch_autotune(self._h, int(steps), _dp(ms))
         if rc < 0:
-            _check_b(rc)
+            _check_b(rc, self._h)
         return ms[:ng]
 
     def close(self):
@@ -406,9 +410,10 @@ class Batch:
             pass
 
 
-def _check_b(rc: int):
-    if rc != PF_OK:
-        raise PfError(rc, "ensemble call failed")
+def _check_b(rc: int, h=None):
+    if rc < 0:
+        msg = load().pf_batch_last_error(h).decode() if h else ""
+        raise PfError(rc, msg or "ensemble call failed")
 
 
 # ---- neural operator (learned warm start) -------------------------------------------------------

@@ -69,13 +69,13 @@ def test_batch_mixed_and_graph_stream():
 def test_batch_autotune_keeps_lockstep():
     runs = uneven_runs()
     b = native.Batch(runs, precision=native.PF_FP64)
-    ms = b.autotune(steps=1)      # one BDF1 step, then 4 x 2 = 8 steps per group
+    ms = b.autotune(steps=1)      # one BDF1 step, then 6 x 2 = 12 steps per group
     assert len(ms) == 3 and np.all(ms > 0)
     oras = [solver_of(wl) for wl in runs]
-    for _ in range(9):
+    for _ in range(13):
         for o in oras:
             o.step()
-    _compare(b, runs, oras, 1e-11, 9)
+    _compare(b, runs, oras, 1e-11, 13)
     b.close()
 
 

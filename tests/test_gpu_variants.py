@@ -13,7 +13,11 @@ from gpu_util import ALL, oracle_fields, rel_errors, run_pair
 pytestmark = pytest.mark.gpu
 
 FP32_VARIANTS = [(native.PF_GEMM_TC, 1), (native.PF_GEMM_PLANE, 1), (native.PF_GEMM_SIMT32, 0),
-                 (native.PF_GEMM_SIMT32, 1), (native.PF_GEMM_SIMT64, 1), (native.PF_GEMM_SIMT32X64, 0)]
+                 (native.PF_GEMM_SIMT32, 1), (native.PF_GEMM_SIMT64, 1), (native.PF_GEMM_SIMT32X64, 0),
+                 (native.PF_GEMM_PIPE64, 0), (native.PF_GEMM_PIPE32, 1), (native.PF_GEMM_PIPE32X64, 0),
+                 (native.PF_GEMM_CLUSTER4, 1), (native.PF_GEMM_CLUSTER2, 1)]
+SIMT = (native.PF_GEMM_SIMT32, native.PF_GEMM_SIMT64, native.PF_GEMM_SIMT32X64, native.PF_GEMM_PIPE64,
+        native.PF_GEMM_PIPE32, native.PF_GEMM_PIPE32X64)
 
 
 def _direct(m, bcset, shift, f):
@@ -79,7 +83,10 @@ def test_set_variant_rejects_what_the_run_cannot_use():
         with pytest.raises(native.PfError) as e:
             h.set_variant(*args)
         assert e.value.code == native.PF_EINVAL
-    gs.set_variant(native.PF_GEMM_PLANE, tile=16)    # FP32 without tensor cores can take the plane solve
+    with pytest.raises(native.PfError):
+        g64.set_variant(native.PF_GEMM_CLUSTER4)
+    gs.set_variant(native.PF_GEMM_CLUSTER2)
+    gs.set_variant(native.PF_GEMM_PLANE, tile=16)    # FP32 without tensor cores can take the plane solves
     gs.step(3)
     g64.set_variant(native.PF_GEMM_SIMT64, fuse_y=False, tile=4)
     g64.step(3)
@@ -87,12 +94,13 @@ def test_set_variant_rejects_what_the_run_cannot_use():
     gs.close()
 
 
-def test_batch_plane_variant_matches_oracle():
+@pytest.mark.parametrize("gemm", [native.PF_GEMM_PLANE, native.PF_GEMM_CLUSTER4])
+def test_batch_plane_variant_matches_oracle(gemm):
     from oracle.runner import solver_of
     from test_gpu_batch import uneven_runs
     runs = uneven_runs()
     b = native.Batch(runs, precision=native.PF_MIXED)
-    b.set_variant(native.PF_GEMM_PLANE)
+    b.set_variant(gemm)
     oras = [solver_of(wl) for wl in runs]
     for _ in range(4):
         for o in oras:
@@ -112,19 +120,56 @@ def test_batch_plane_variant_matches_oracle():
 @pytest.mark.parametrize("with_stream", [True, False])
 def test_autotune_advances_the_stated_steps_and_keeps_parity(with_stream):
     """pf_autotune times every variant (graph replays on a stream of its own, eager launches on the
-    legacy stream), advances the run by 10 (steps + 2) steps, and the run stays on the FP64 oracle."""
+    legacy stream), advances the run by 15 (steps + 2) steps, and the run stays on the FP64 oracle."""
     from oracle.runner import solver_of
     torch = pytest.importorskip("torch")
     wl = workloads.small3d(ex=4, ey=2, order=4, nz=8)
     s = torch.cuda.Stream() if with_stream else None
     g = native.from_workload(wl, precision=native.PF_FP64, stream=s.cuda_stream if s is not None else None)
     choice, ms = g.autotune(steps=1)
-    assert ms > 0 and choice % 1000 in (native.PF_GEMM_SIMT32, native.PF_GEMM_SIMT64, native.PF_GEMM_SIMT32X64)
-    assert choice // 1000 in (4, 8, 16, 32)
+    assert ms > 0 and choice % 1000 in SIMT
+    assert choice // 1000 in (0, 4, 8, 16, 32)
     g.step(3)
     ora = solver_of(wl)
-    for _ in range(1 + 10 * 3 + 3):
+    for _ in range(1 + 15 * 3 + 3):
         ora.step()
     errs = rel_errors(g.get(ALL), oracle_fields(ora))
     g.close()
     assert all(v <= 1e-11 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("nz", [1, 8])
+def test_fp64_cuda_core_variants_agree_bit_for_bit(nz):
+    """In FP64 every CUDA-core transform variant sums in sequential k order: identical bits (for
+    each choice of the y pair, whose fused form adds the eigenvalue sum in another order)."""
+    wl = workloads.small3d(ex=5, ey=3, order=5, nz=nz) if nz > 1 else workloads.small2d(ex=5, ey=3, order=5)
+    for fuse_y in (0, 1):
+        ref = None
+        for gemm in SIMT:
+            g = native.from_workload(wl, precision=native.PF_FP64)
+            g.set_variant(gemm, fuse_y=bool(fuse_y))
+            g.step(4)
+            f = g.get(ALL)
+            g.close()
+            if ref is None:
+                ref = f
+            for k in f:
+                assert np.array_equal(f[k], ref[k]), (gemm, fuse_y, k)
+
+
+@pytest.mark.parametrize("gemm", [native.PF_GEMM_CLUSTER4, native.PF_GEMM_PLANE, native.PF_GEMM_PIPE32])
+def test_variant_graph_replay_is_bit_identical(gemm):
+    """A pinned variant replayed from the captured graphs gives the bits of eager launches."""
+    torch = pytest.importorskip("torch")
+    wl = workloads.small3d(ex=4, ey=2, order=4, nz=8)
+    s = torch.cuda.Stream()
+    a = native.from_workload(wl, precision=native.PF_MIXED, stream=s.cuda_stream)
+    b = native.from_workload(wl, precision=native.PF_MIXED)
+    for h in (a, b):
+        h.set_variant(gemm, tile=8)
+        h.step(6)
+    fa, fb = a.get(ALL), b.get(ALL)
+    a.close()
+    b.close()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
