@@ -123,6 +123,25 @@ class ClockSampler:
 
 
 # ---- algorithmic work per kernel class ----------------------------------------------------------
+def transform_kernel(code, fused_y):
+    """Kernel(s) of the chosen transform variant (PF_GEMM_* code)."""
+    name = {0: "k_gemm_tc", 1: "k_fdm_plane", 6: "k_fdm_cluster<4>", 7: "k_fdm_cluster<2>"}.get(
+        code, "k_gemm_cp" if code in (3, 4, 5) else "k_gemm")
+    return name + (" + k_fdm_y" if fused_y and code not in (0, 1, 6, 7) else "")
+
+
+# DRAM traffic per launch of a transform kernel on droplet3d, from one ncu capture of an unchanged
+# kernel (profiles/k_gemm_cp_droplet3d.md): (precision, variant code, fused y) -> bytes
+TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("mixed", 4, 0): 2.24e6}
+
+
+def transform_bytes_per_launch(nx, ny, nz, prec):
+    """Algorithmic bytes of one transform GEMM launch of a scalar solve: read the planes and the
+    eigenbasis, write the planes."""
+    w = 8 if prec == 0 else 4
+    return w * (2 * nx * ny * nz + max(nx, ny) ** 2)
+
+
 def fdm_flops_per_step(nx, ny, nz, d3):
     """Fast-diagonalisation flops of one step: 4 n2 (n_x + n_y) per real plane and solve
     (two GEMM passes each way); planes: V, psi, phi, P (Nz each) and d velocity components."""
@@ -173,6 +192,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="pin the transform variant (a PF_GEMM_* code) instead of autotuning")
+    ap.add_argument("--fused-y", type=int, default=0, help="with --variant: run the y pair fused (1) or not (0)")
+    ap.add_argument("--fft-tile", type=int, default=0, help="with --variant: pencils per z-transform block (0: heuristic)")
     ap.add_argument("--warmstart", action="store_true", help="learned warm start study instead (minutes)")
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
@@ -215,8 +238,12 @@ def main():
             dist.barrier()
 
     h.step(args.warmup)
-    tuned, _ = h.autotune(steps=5)   # fastest transform GEMM and z-transform tile (advances the run)
-    gemm_choice, fft_tile = tuned % 1000, tuned // 1000
+    if args.variant is None:
+        tuned, _ = h.autotune(steps=5)   # fastest transform variant, y pair, z-transform tile (advances the run)
+        gemm_choice, fft_tile, fused_y = tuned % 1000, (tuned // 1000) % 100, tuned // 100000
+    else:
+        h.set_variant(args.variant, fuse_y=bool(args.fused_y), tile=args.fft_tile)
+        gemm_choice, fft_tile, fused_y = args.variant, args.fft_tile, args.fused_y
     h.step(2)
     barrier()
     launches0 = h.profile_read()
@@ -269,14 +296,19 @@ def main():
                                        "counts the FP32 GEMM flops, 3 TF32 MMAs are issued per useful product"}
             elif prec != native.PF_FP64:
                 peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-                roof = {"bound": "alu", "kernel": "k_gemm (FP32 SIMT fast-diagonalisation transforms)",
+                roof = {"bound": "alu", "kernel": transform_kernel(gemm_choice, fused_y) + " (FP32 SIMT transforms)",
                         "peak_source": f"derived: {SM_COUNT} SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
             else:
                 peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-                roof = {"bound": "alu", "kernel": "k_gemm (FP64 SIMT fast-diagonalisation transforms)",
+                roof = {"bound": "alu", "kernel": transform_kernel(gemm_choice, fused_y) + " (FP64 SIMT transforms)",
                         "peak_source": f"derived: {SM_COUNT} SMs x 2 FP64 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+            traffic = TRANSFORM_DRAM_BYTES_PER_LAUNCH.get((args.precision, gemm_choice, fused_y))
             roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None})
+                         "traffic": traffic,
+                         "traffic_note": None if traffic is None else
+                         "DRAM bytes per transform launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                         "mean of one solve's four launches on this workload, profiles/); algorithmic "
+                         f"{transform_bytes_per_launch(nx, ny, nz, prec):.3e} B per launch"})
         else:
             roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": None, "peak_source": src}
@@ -322,7 +354,8 @@ def main():
                                     4: "SIMT 32x32 tiles, cp.async pipeline", 5: "SIMT 32x64 tiles, cp.async pipeline",
                                     6: "whole solve per plane on a 4-block cluster (SIMT, distributed shared memory)",
                                     7: "whole solve per plane on a 2-block cluster (SIMT, distributed shared memory)"}.get(gemm_choice, f"SIMT {gemm_choice}x{gemm_choice} tiles")
-                                   + " (autotuned)",
+                                   + (", y pair fused" if fused_y and gemm_choice not in (0, 1, 6, 7) else "")
+                                   + (" (autotuned)" if args.variant is None else " (pinned)"),
                        "fft_pencils_per_block": fft_tile,
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": gpu_launches, "clocks": clocks}

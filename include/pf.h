@@ -244,8 +244,9 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
  * run fused (one pass, eigenbasis in shared memory), then (3D) the z-transform tile of 4, 8, 16
  * or 32 pencils per block.  Each candidate is timed as the run executes its steady steps: graph
  * replays when the run has its own stream, eager launches on the legacy stream.  The run advances
- * by 15 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile with gemm a PF_GEMM_*
- * code and tile = 0 in 2D; ms_per_step (nullable) the best time. */
+ * by 15 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile + 100000 * fused_y with
+ * gemm a PF_GEMM_* code, tile the pencils per z-transform block (0: size heuristic, always 0 in
+ * 2D) and fused_y 1 when the y pair runs fused; ms_per_step (nullable) the best time. */
 int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);
 
 /* Pin the transform variant without timing (to reproduce an autotuned choice or to compare

@@ -1434,7 +1434,7 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
     }
     drop_graphs();
     for (; taken < total; ++taken) E.step(2);
-    if (choice) *choice = pick + 1000 * E.tp_override;
+    if (choice) *choice = pick + 1000 * E.tp_override + ((E.fuse_y && !E.fuse_plane && !E.cluster) ? 100000 : 0);
     if (best_ms) *best_ms = best;
 }
 }  // namespace

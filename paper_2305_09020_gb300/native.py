@@ -266,7 +266,8 @@ class Solver:
         return out
 
     def autotune(self, steps: int = 5):
-        """Pick the fastest transform GEMM and z-transform tile; returns (gemm + 1000 * tile, ms/step)."""
+        """Pick the fastest transform variant, y pair and z-transform tile; returns
+        (gemm + 1000 * tile + 100000 * fused_y, ms/step)."""
         ch = c_int()
         ms = np.zeros(1)
         _check(load().pf_autotune(self._h, int(steps), ctypes.byref(ch), _dp(ms)), self._h)
