@@ -20,7 +20,7 @@ def solver_of(wl, init=True, **kw) -> Solver:
     m = wl.mesh
     mesh = Mesh2D(m.xb, m.yb, m.order)
     v = wl.vbc
-    sol = Solver(mesh, params_of(wl, **kw), VBC(v.bottom_kind, v.top_kind, v.v_bottom, v.v_top),
+    sol = Solver(mesh, params_of(wl, **kw), VBC(v.bottom_kind, v.top_kind, v.v_bottom, v.v_top, tuple(getattr(v, 'patches', ()))),
                  nz=m.nz, lz=m.lz)
     if init:
         Zg, Yg, Xg = np.meshgrid(sol.zc, mesh.Y, mesh.X, indexing="ij")

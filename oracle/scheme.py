@@ -38,6 +38,12 @@ Readings of the paper taken here (each also listed in the design notes):
   gamma1 dt)) with gamma0 of the run's BDF order; a discriminant below 1e-10
   in the formula for alpha is set to 0.
 
+Electrode patches (eq. 21, NEXT to the whole-side conditions): with VBC(bottom_kind=PATCHES) the
+wall nodes whose x lies on an electrode interval (closed, or its periodic image) are Dirichlet
+nodes holding that electrode's voltage, and the other wall nodes are free (the natural condition
+dV/dn = 0 of the gaps); the electrodes are uniform in z (stripes along z, as in Sec. 4's set-up),
+so in 3D only mode 0 carries the electrode voltages.
+
 With ``Params(equilibrium=True)`` the step is that of the simpler equilibrium system of Sec. 2.4
 (eq. 16 with eq. 15c, 15d): the V and phi sub-steps with u = 0; P and u are not computed.
 
@@ -45,7 +51,9 @@ Parity status: pinned by tests/test_oracle_scheme.py (manufactured solutions
 of eq. 80/81 converge spectrally in K and at second order in dt; reduction
 consistency for phi = 1; series-capacitor potential of flat layers; discrete
 phase-mass identity; energy decay at zero voltage; zero velocity for a flat
-interface at rest).
+interface at rest) and tests/test_oracle_patches.py (patches reduce to whole-side conditions;
+symmetries of an alternating array; a manufactured potential with dV/dy = 0 on the gaps converges
+spectrally).
 """
 from __future__ import annotations
 
@@ -60,6 +68,7 @@ from .sem import Mesh2D
 
 DIRICHLET = 0
 NEUMANN = 1
+PATCHES = 2     # wall only: electrodes (Dirichlet) on x-intervals, natural condition on the gaps
 
 
 @dataclass
@@ -133,11 +142,25 @@ class Params:
 
 @dataclass
 class VBC:
-    """Whole-side potential boundary conditions (bottom wall, top)."""
+    """Potential boundary conditions of eq. (21) and (a25): each side Dirichlet or Neumann as a
+    whole, or (wall only) PATCHES: V = V_e on the electrodes, dV/dn = 0 on the gaps between them.
+    ``patches`` lists (x0, x1, V_e) per electrode; a wall node is on an electrode when its x lies
+    in the closed interval (to 1e-9 of the interval length plus 1e-12; x or its periodic image)."""
     bottom_kind: int = DIRICHLET
     top_kind: int = NEUMANN
     v_bottom: float = 0.0
     v_top: float = 0.0
+    patches: tuple = ()
+
+
+def electrode_of(x, patches, period):
+    """Index of the electrode (x0, x1, V) holding wall coordinate x (or its periodic image
+    x + period), or -1 on a gap."""
+    for e, (x0, x1, _) in enumerate(patches):
+        tol = 1e-9 * abs(x1 - x0) + 1e-12
+        if x0 - tol <= x <= x1 + tol or x0 - tol <= x + period <= x1 + tol:
+            return e
+    return -1
 
 
 def _zeros_like_rows(nz, nx):
@@ -222,12 +245,26 @@ class Solver:
         return [self.gx(f), self.gy(f), self.loc(self.dz(f))]
 
     # ---- linear solves ---------------------------------------------------------------------
+    def _electrode_columns(self):
+        """x-indices of the wall nodes on electrodes, and their voltages (PATCHES only)."""
+        m = self.mesh
+        period = m.xb[-1] - m.xb[0]
+        cols, vals = [], []
+        for j, x in enumerate(m.X):
+            e = electrode_of(x, self.vbc.patches, period)
+            if e >= 0:
+                cols.append(j)
+                vals.append(self.vbc.patches[e][2])
+        return np.array(cols, dtype=int), np.array(vals)
+
     def _dirichlet_nodes(self, kind):
         m = self.mesh
         if kind == "V":
             nodes = []
             if self.vbc.bottom_kind == DIRICHLET:
                 nodes.append(m.bottom_nodes)
+            elif self.vbc.bottom_kind == PATCHES:
+                nodes.append(m.bottom_nodes[self._electrode_columns()[0]])
             if self.vbc.top_kind == DIRICHLET:
                 nodes.append(m.top_nodes)
             return np.concatenate(nodes) if nodes else np.zeros(0, dtype=int)
@@ -270,7 +307,13 @@ class Solver:
                    g2_top=s.get("g2_top", zr), g3_bot=s.get("g3_bot", zr),
                    f1_top=s.get("f1_top", [zr, zr, zr]), f2_top=s.get("f2_top", zr),
                    w_bot=s.get("w_bot", [zr, zr, zr]))
-        vb = s.get("V_bot", np.full((self.nz, m.nx), self.vbc.v_bottom))
+        if self.vbc.bottom_kind == PATCHES:
+            cols, vals = self._electrode_columns()
+            vb0 = np.zeros((self.nz, m.nx))
+            vb0[:, cols] = vals
+        else:
+            vb0 = np.full((self.nz, m.nx), self.vbc.v_bottom)
+        vb = s.get("V_bot", vb0)
         vt = s.get("V_top", np.full((self.nz, m.nx), self.vbc.v_top))
         out["V_bot"], out["V_top"] = vb, vt
         return out
@@ -280,6 +323,8 @@ class Solver:
         parts = []
         if self.vbc.bottom_kind == DIRICHLET:
             parts.append(self.fft(s["V_bot"]))
+        elif self.vbc.bottom_kind == PATCHES:
+            parts.append(self.fft(s["V_bot"][:, self._electrode_columns()[0]]))
         if self.vbc.top_kind == DIRICHLET:
             parts.append(self.fft(s["V_top"]))
         if not parts:

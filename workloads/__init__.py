@@ -49,9 +49,12 @@ class Fluid:
     theta_s_deg: float = 90.0
 
 
-# Boundary-condition kinds for the potential on a whole side of the domain.
+# Boundary-condition kinds for the potential on a side of the domain.  BC_PATCHES (wall only):
+# electrodes on parts of the wall (Dirichlet, one voltage per electrode), zero normal derivative on
+# the gaps between them; electrodes are x-intervals, uniform in z (stripes along z in 3D).
 BC_DIRICHLET = 0
 BC_NEUMANN = 1
+BC_PATCHES = 2
 
 
 @dataclasses.dataclass
@@ -60,6 +63,7 @@ class VoltageBC:
     top_kind: int = BC_NEUMANN
     v_bottom: float = 0.0
     v_top: float = 0.0
+    patches: tuple = ()     # with BC_PATCHES: ((x0, x1, voltage), ...), closed x-intervals
 
 
 @dataclasses.dataclass
@@ -212,6 +216,33 @@ def small2d(ex: int = 4, ey: int = 2, order: int = 5, eta: float = 0.08,
                     sigma=1.0, eta=eta, gamma1=1e-3, theta_s_deg=theta_s_deg),
         vbc=VoltageBC(BC_DIRICHLET, v_top_kind, v_bottom=1.0, v_top=0.0),
         scheme=Scheme(dt=1e-3),
+        steps=10,
+        phi0=phi0,
+    )
+
+
+def patches2d(ex: int = 16, ey: int = 4, order: int = 8, nz: int = 1, v0: float = 1.5,
+              eta: float = 0.02, top_kind: int = BC_NEUMANN, dt: float = 1e-4) -> Workload:
+    """Electrodes on part of the wall (the four-electrode drop of Sec. 4 in normalised units):
+    domain [0, 1.6] x [0, 0.5] (x [0, 1) in 3D), electrodes on x in [0.1, 0.2], [0.3, 0.4],
+    [0.5, 0.6], [0.7, 0.8] at -v0, +v0, -v0, +v0, zero normal derivative of V on the gaps and on
+    the open top; a half-disc (3D: half-ball) drop of radius 0.35 centred on the wall at x = 1.2."""
+
+    def phi0(x, y, z):
+        r2 = (x - 1.2) ** 2 + y ** 2
+        if nz > 1:
+            r2 = r2 + (z - 0.5) ** 2
+        return _tanh_profile(0.35 - np.sqrt(r2), eta)
+
+    pats = ((0.1, 0.2, -v0), (0.3, 0.4, v0), (0.5, 0.6, -v0), (0.7, 0.8, v0))
+    return Workload(
+        name=f"patches_{ex}x{ey}_K{order}_nz{nz}",
+        mesh=Mesh(xb=np.linspace(0.0, 1.6, ex + 1), yb=np.linspace(0.0, 0.5, ey + 1), order=order,
+                  nz=nz, lz=1.0),
+        fluid=Fluid(rho1=2.0, rho2=1.0, mu1=2.0, mu2=1.0, eps1=5.0, eps2=1.0,
+                    sigma=1.0, eta=eta, gamma1=1e-3, theta_s_deg=90.0),
+        vbc=VoltageBC(BC_PATCHES, top_kind, v_bottom=0.0, v_top=0.0, patches=pats),
+        scheme=Scheme(dt=dt),
         steps=10,
         phi0=phi0,
     )
