@@ -50,6 +50,7 @@ extern "C" {
 /* ---- enumerations ---------------------------------------------------------------------- */
 #define PF_BC_DIRICHLET 0
 #define PF_BC_NEUMANN   1
+#define PF_BC_PATCHES   2   /* wall only: electrodes on parts of the wall (eq. 21), see pf_vbc */
 
 #define PF_FP64  0   /* every kernel in double precision                                  */
 #define PF_MIXED 1   /* node-wise kernels and FFT in FP32, eigenbasis GEMMs in 3xTF32 on   */
@@ -94,9 +95,20 @@ typedef struct {
     double theta_s_deg;    /* static contact angle on the wall, eq. theta_def (90 = none)  */
 } pf_fluid;
 
+/* Potential boundary conditions (eq. 21 on the wall, eq. a25 or a Dirichlet top).  Each side is
+ * Dirichlet (an electrode over the whole side, voltage v_bottom / v_top) or Neumann (dV/dn = 0);
+ * the wall may instead carry electrode patches, bottom_kind = PF_BC_PATCHES: n_patch electrodes on
+ * the closed x-intervals [patch_x0[e], patch_x1[e]] (uniform in z: stripes along z in 3D) at
+ * voltage patch_v[e], and dV/dn = 0 on the gaps.  A wall node is on electrode e when its x (or
+ * x + the x-period) lies in the interval to 1e-9 of its length plus 1e-12.  The patch arrays are
+ * host memory, read during pf_create only, and ignored for other kinds.  The patch solve is the
+ * base solve with the whole wall Dirichlet plus a capacitance (Schur-complement) correction on
+ * the gap nodes, per Fourier mode: two fast-diagonalisation solves per potential solve. */
 typedef struct {
-    int bottom_kind, top_kind;   /* PF_BC_DIRICHLET (electrode) or PF_BC_NEUMANN (gap)     */
+    int bottom_kind, top_kind;   /* PF_BC_DIRICHLET, PF_BC_NEUMANN, or PF_BC_PATCHES (wall)  */
     double v_bottom, v_top;      /* electrode voltages for Dirichlet sides                 */
+    int n_patch;                 /* PF_BC_PATCHES: number of electrodes (>= 0)              */
+    const double *patch_x0, *patch_x1, *patch_v;   /* PF_BC_PATCHES: n_patch each          */
 } pf_vbc;
 
 typedef struct {
@@ -149,7 +161,9 @@ int pf_fdm_1d(int n, const double *Kmat, const double *Mdiag, const unsigned cha
  * consecutive blocks ux,uy,uz, nullable -> 0), P^0 = 0, compute V^0 by the fixed
  * point of the Remark in Sec. 3.1 (FP64 on the device) and E^0.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
- * Errors: PF_EINVAL (bad descriptor), PF_ENOMEM, PF_ECUDA. *out is NULL on error. */
+ * Errors: PF_EINVAL (bad descriptor, including patch intervals that are not finite with
+ * x0 <= x1, PF_BC_PATCHES on the top, or a potential with no Dirichlet node at all),
+ * PF_ENOMEM, PF_ECUDA. *out is NULL on error. */
 int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc,
               const pf_scheme *scheme, const double *phi0, const double *u0,
               void *cuda_stream, pf_handle **out);

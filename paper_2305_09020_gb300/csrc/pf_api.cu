@@ -64,6 +64,12 @@ struct HostSetup {
     std::vector<double> liftV;                   // K_y[:, D] * V_D (potential lifting)
     int vrow0 = -1, vrow1 = -1;                  // Dirichlet rows of the potential
     double v0 = 0, v1 = 0;
+    // electrode patches on the wall (eq. 21): intervals and voltages; gap nodes and the
+    // capacitance (Schur-complement) inverses of the gap rows, one m x m block per mode plane
+    bool patch = false;
+    std::vector<double> px0, px1, pv;
+    std::vector<int> gapj, gapidx;               // gap node x-indices; x-index -> gap index or -1
+    std::vector<double> vbx, Ky0, Cinv;          // wall voltages (0 on gaps), K_y[0][:], C^-1 per plane
     // physics
     double rho1, rho2, mu1, mu2, eps1, eps2, sigma, eta, gamma1, theta;
     double dt, S, nu_m, rho0, eps0, lam, cos_theta;
@@ -165,6 +171,11 @@ struct Engine {
     T *liftV;
     cplx<T> *tw;
     T *shV, *shP, *shPsi[2], *shPhi[2], *shU[2], *shTmp;
+    // electrode patches: gap tables, wall voltages, capacitance inverses, gap values per plane
+    int npatch_gap = 0;
+    int *gapj = nullptr, *gapidx = nullptr;
+    T *Ky0 = nullptr, *Kxd = nullptr, *Cinv = nullptr, *gbuf = nullptr;
+    T *wallw = nullptr;   // wall values per mode plane [nz][nx]: electrode voltages (plane 0), last gap values
     // state: level slots [0], [1]; cur = slot of level n
     T *V[2], *Ez[2], *phi[2], *dzphi[2], *P[2], *dzP[2], *u[3][2], *dzu[3][2];
     T *Ex, *Ey, *W, *dzW, *Lf, *Q2;
@@ -263,6 +274,20 @@ struct Engine {
             Ly[b] = up(s.Ly[b]);
         }
         liftV = up(s.liftV);
+        if (s.patch) {
+            npatch_gap = (int)s.gapj.size();
+            gapj = mk<int>(std::max(1, npatch_gap));
+            gapidx = mk<int>(nx);
+            if (npatch_gap > 0)
+                PF_CU(cudaMemcpyAsync(gapj, s.gapj.data(), s.gapj.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            PF_CU(cudaMemcpyAsync(gapidx, s.gapidx.data(), s.gapidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            PF_CU(cudaStreamSynchronize(st));
+            Ky0 = up(s.Ky0); Kxd = up(s.Kx); Cinv = up(s.Cinv);
+            gbuf = mk<T>((size_t)nz * std::max(1, npatch_gap));
+            std::vector<double> w0((size_t)nz * nx, 0.0);
+            std::copy(s.vbx.begin(), s.vbx.end(), w0.begin());
+            wallw = up(w0);
+        }
         if (indep) {
             std::vector<double> e0(nz), sc(nz), lb(ny, 0.0), lt(ny, 0.0);
             for (int q = 0; q < nz; ++q) {
@@ -653,8 +678,9 @@ struct Engine {
     }
 
     void fwd(const T *X0, int x0l, const T *X1, int x1l, int mult, double scale, const T *lift, T *out,
-             T *out1, int ncomp = 1) {
+             T *out1, int ncomp = 1, const T *lift2y = nullptr, const T *lift2x = nullptr) {
         pf::FwdArgs<T> a;
+        a.lift2y = lift2y; a.lift2x = lift2x;
         a.cs_x0 = x0l ? NL : N; a.cs_x1 = x1l ? NL : N; a.cs_out = N;
         a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
@@ -727,10 +753,36 @@ struct Engine {
         check_launch();
         prof->end(st);
         if (indep) fwd_indep(LA, nullptr, pscale, true, RHS, nullptr);
+        else if (hs.patch) fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr, 1, Ky0, wallw);
         else fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_V, shV, nz);
+        if (hs.patch) patch_correction();
         if (indep) inv_indep(OUT, Vout, true, false, 0.0);
+        else if (hs.patch) inv(OUT, Vout, Ezout, -1, 0.0, hs.vrow1, hs.v1);
         else inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
+    }
+
+    // Electrode patches (eq. 21): OUT holds the base solve y with the whole wall Dirichlet at the
+    // values w = wallw (electrode voltages in mode 0, the previous solve's gap values).  The gap
+    // change d = C^-1 (b_G - A_G,wall w - A_GI y) per plane, the correction z = A_II^-1 A_IG d
+    // (second solve), then V = y - z off the wall and w + d on the wall; w keeps the new gap
+    // values.  Starting from the last gap values keeps d and z small, so that y - z loses few digits.
+    void patch_correction() {
+        const int m = npatch_gap;
+        T *rhs2 = RHS + N, *z = OUT + N;
+        if (m > 0) {
+            prof->begin(PF_KC_OTHER, st);
+            pf::k_cap_solve<T><<<nz, 256, (size_t)2 * m * sizeof(T), st>>>(
+                geo(), RHS, OUT, gapj, gapidx, m, wallw, Kxd, Ky0, (T)hs.My[0], shV, Cinv, gbuf, rhs2);
+            check_launch();
+            prof->end(st);
+            fdm(rhs2, z, PF_BCSET_V, shV, nz);
+        }
+        prof->begin(PF_KC_OTHER, st);
+        pf::k_cap_combine<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(geo(), OUT, m > 0 ? z : nullptr, gbuf,
+                                                                        gapidx, m, wallw, OUT, N);
+        check_launch();
+        prof->end(st);
     }
 
     void efield(const T *Vf) {
@@ -881,6 +933,8 @@ int cuda_fail(pf_handle *h, const CudaError &e) {
     return fail(h, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
 }
 
+void build_patches(HostSetup &s);
+
 void build_setup(HostSetup &s) {
     s.p = s.K + 1;
     s.nx = s.ex * s.K;
@@ -931,6 +985,108 @@ void build_setup(HostSetup &s) {
     s.Y.resize(ny);
     for (int e = 0; e < s.ey; ++e)
         for (int b = 0; b <= s.K; ++b) s.Y[e * s.K + b] = s.yb[e] + 0.5 * (s.xi[b] + 1.0) * s.hy[e];
+    if (s.patch) build_patches(s);
+}
+
+// Electrode patches (eq. 21): classify the wall nodes, and for every mode plane build the
+// capacitance matrix of the gap rows and invert it (FP64).  With A the plane operator
+// K_x (x) M_y + M_x (x) K_y + c M_x (x) M_y and the base solve A_II^-1 on everything but the wall
+// row, the gap values g solve C g = b_G - A_GE V_E - A_GI A_II^-1 (b_I - A_IE V_E) with
+// C = A_GG - A_GI A_II^-1 A_IG.  A_IG couples a gap node (0, j) only with (i, j), i >= 1, through
+// M_x[j] K_y[i][0], so in the base eigenbases (S_x, L_x; S_y, L_y of the Dirichlet-wall set)
+//   (A_GI A_II^-1 A_IG)[j][l] = M_x[j] M_x[l] sum_a S_x[j][a] S_x[l][a] sum_b w_b^2 / (L_x[a] + L_y[b] + c),
+// w_b = sum_i K_y[0][i] S_y[i][b]; A_GG[j][l] = M_y[0] K_x[j][l] + [j = l] M_x[j] (K_y[0][0] + c M_y[0]).
+int electrode_at(const HostSetup &s, double x) {
+    const double period = s.xb[s.ex] - s.xb[0];
+    for (size_t e = 0; e < s.px0.size(); ++e) {
+        const double tol = 1e-9 * std::fabs(s.px1[e] - s.px0[e]) + 1e-12;
+        if ((x >= s.px0[e] - tol && x <= s.px1[e] + tol) || (x + period >= s.px0[e] - tol && x + period <= s.px1[e] + tol))
+            return (int)e;
+    }
+    return -1;
+}
+
+// in-place inverse of a dense n x n matrix (Gauss-Jordan, partial pivoting); false if singular
+bool invert_dense(std::vector<double> &A, int n) {
+    std::vector<double> I((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+        if (A[(size_t)piv * n + c] == 0.0) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+                std::swap(I[(size_t)c * n + k], I[(size_t)piv * n + k]);
+            }
+        const double d = 1.0 / A[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) { A[(size_t)c * n + k] *= d; I[(size_t)c * n + k] *= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+                I[(size_t)r * n + k] -= f * I[(size_t)c * n + k];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+void build_patches(HostSetup &s) {
+    const int nx = s.nx, ny = s.ny, nz = s.nz;
+    s.vbx.assign(nx, 0.0);
+    s.gapidx.assign(nx, -1);
+    s.gapj.clear();
+    for (int j = 0; j < nx; ++j) {
+        const int e = electrode_at(s, s.X[j]);
+        if (e >= 0) s.vbx[j] = s.pv[e];
+        else { s.gapidx[j] = (int)s.gapj.size(); s.gapj.push_back(j); }
+    }
+    const int m = (int)s.gapj.size();
+    s.Ky0.assign(s.Ky.begin(), s.Ky.begin() + ny);   // row 0 (= column 0, K_y is symmetric)
+    const std::vector<double> &Sy = s.Sy[PF_BCSET_V], &Ly = s.Ly[PF_BCSET_V];
+    std::vector<double> w2(ny, 0.0);
+    for (int b = 0; b < ny; ++b) {
+        double acc = 0.0;
+        for (int i = 0; i < ny; ++i) acc += s.Ky0[i] * Sy[(size_t)i * ny + b];
+        w2[b] = acc * acc;
+    }
+    s.Cinv.assign((size_t)nz * m * m, 0.0);
+    std::vector<double> gam(nx), C((size_t)m * m);
+    int done_k = -1;
+    std::vector<double> last;
+    for (int p = 0; p < nz; ++p) {
+        int k = 0;
+        if (nz > 1) k = (p == 0) ? 0 : (p == 1 ? nz / 2 : p / 2);
+        if (k == done_k) {   // planes 2k and 2k+1 share the mode
+            std::copy(last.begin(), last.end(), s.Cinv.begin() + (size_t)p * m * m);
+            continue;
+        }
+        const double beta = nz > 1 ? 2.0 * M_PI * k / s.lz : 0.0;
+        const double c = beta * beta;
+        for (int a = 0; a < nx; ++a) {
+            double acc = 0.0;
+            for (int b = 0; b < ny; ++b) acc += w2[b] / (s.Lx[a] + Ly[b] + c);
+            gam[a] = acc;
+        }
+        for (int jj = 0; jj < m; ++jj)
+            for (int ll = 0; ll < m; ++ll) {
+                const int j = s.gapj[jj], l = s.gapj[ll];
+                double acc = 0.0;
+                for (int a = 0; a < nx; ++a) acc += s.Sx[(size_t)j * nx + a] * s.Sx[(size_t)l * nx + a] * gam[a];
+                double v = s.My[0] * s.Kx[(size_t)j * nx + l] - s.Mx[j] * s.Mx[l] * acc;
+                if (jj == ll) v += s.Mx[j] * (s.Ky[0] + c * s.My[0]);
+                C[(size_t)jj * m + ll] = v;
+            }
+        if (m > 0 && !invert_dense(C, m)) C.assign((size_t)m * m, NAN);
+        std::copy(C.begin(), C.end(), s.Cinv.begin() + (size_t)p * m * m);
+        last = C;
+        done_k = k;
+    }
 }
 
 // initial potential: fixed point of the Remark in Sec. 3.1 in FP64, run to the round-off
@@ -1056,8 +1212,22 @@ int fill_setup(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, co
         if (!(mesh->xb[e + 1] > mesh->xb[e])) return bad("xb must increase");
     for (int e = 0; e < mesh->ey; ++e)
         if (!(mesh->yb[e + 1] > mesh->yb[e])) return bad("yb must increase");
-    if (vbc->bottom_kind != PF_BC_DIRICHLET && vbc->bottom_kind != PF_BC_NEUMANN) return bad("bad bottom_kind");
+    if (vbc->bottom_kind != PF_BC_DIRICHLET && vbc->bottom_kind != PF_BC_NEUMANN &&
+        vbc->bottom_kind != PF_BC_PATCHES)
+        return bad("bad bottom_kind");
     if (vbc->top_kind != PF_BC_DIRICHLET && vbc->top_kind != PF_BC_NEUMANN) return bad("bad top_kind");
+    if (vbc->bottom_kind == PF_BC_PATCHES) {
+        if (vbc->n_patch < 0 || (vbc->n_patch > 0 && (!vbc->patch_x0 || !vbc->patch_x1 || !vbc->patch_v)))
+            return bad("bad electrode patch arrays");
+        for (int e = 0; e < vbc->n_patch; ++e)
+            if (!std::isfinite(vbc->patch_x0[e]) || !std::isfinite(vbc->patch_x1[e]) ||
+                !std::isfinite(vbc->patch_v[e]) || vbc->patch_x0[e] > vbc->patch_x1[e])
+                return bad("electrode patches need finite x0 <= x1 and a finite voltage");
+        s.patch = true;
+        s.px0.assign(vbc->patch_x0, vbc->patch_x0 + vbc->n_patch);
+        s.px1.assign(vbc->patch_x1, vbc->patch_x1 + vbc->n_patch);
+        s.pv.assign(vbc->patch_v, vbc->patch_v + vbc->n_patch);
+    }
     if (vbc->bottom_kind == PF_BC_NEUMANN && vbc->top_kind == PF_BC_NEUMANN)
         return bad("the potential needs an electrode (Dirichlet) on at least one side");
     const pf_fluid &f = *fluid;
@@ -1086,6 +1256,7 @@ int fill_setup(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, co
     }
     s.cos_theta = std::cos(s.theta * M_PI / 180.0);
     if (vbc->bottom_kind == PF_BC_DIRICHLET) { s.vrow0 = 0; s.v0 = vbc->v_bottom; }
+    if (vbc->bottom_kind == PF_BC_PATCHES) { s.vrow0 = 0; s.v0 = 0.0; }   // base solve: the whole wall Dirichlet
     if (vbc->top_kind == PF_BC_DIRICHLET) { s.vrow1 = s.ey * s.K; s.v1 = vbc->v_top; }
     return PF_OK;
 }
@@ -1117,6 +1288,8 @@ int build_engines(const HostSetup &s, const double *phi0, const double *u0, cuda
         for (int c = 0; c < 3; ++c) { cv(e64->u[c][l], e32->u[c][l]); cv(e64->dzu[c][l], e32->dzu[c][l]); }
     }
     cv(e64->Ex, e32->Ex); cv(e64->Ey, e32->Ey);
+    if (e64->wallw && e32->wallw)
+        pf::k_convert<double, float><<<64, 256, 0, st>>>(e64->wallw, e32->wallw, (long long)e64->nz * e64->nx);
     PF_CU(cudaGetLastError());
     PF_CU(cudaStreamSynchronize(st));
     e64.reset();
@@ -1135,6 +1308,9 @@ extern "C" int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vb
     int rc = fill_setup(mesh, fluid, vbc, scheme, h->hs, err);
     if (rc != PF_OK) return fail(nullptr, rc, err);
     build_setup(h->hs);
+    if (h->hs.patch && (int)h->hs.gapj.size() == h->hs.nx && h->hs.vrow1 < 0)
+        return fail(nullptr, PF_EINVAL, "no wall node lies on an electrode and the top is not Dirichlet: "
+                                        "the potential is undetermined");
     h->st = (cudaStream_t)cuda_stream;
     try {
         rc = build_engines(h->hs, phi0, u0, h->st, &h->prof, h->e64, h->e32, h->v_iters, err);
@@ -1632,6 +1808,8 @@ extern "C" int pf_batch_create(int nrun, const pf_mesh *meshes, const pf_fluid *
     std::vector<HostSetup> setups(nrun);
     for (int r = 0; r < nrun; ++r) {
         std::string err;
+        if (vbcs[r].bottom_kind == PF_BC_PATCHES)
+            return fail(nullptr, PF_EINVAL, "electrode patches are not supported in ensembles");
         const int rc = fill_setup(&meshes[r], &fluids[r], &vbcs[r], scheme, setups[r], err);
         if (rc != PF_OK) return fail(nullptr, rc, "run " + std::to_string(r) + ": " + err);
         if (meshes[r].nz != 1) return fail(nullptr, PF_EINVAL, "ensemble runs must be 2D (nz = 1)");

@@ -553,6 +553,7 @@ struct FwdArgs {
     int mult;                       // 0: X0 + i beta X1 ; 1: X0 + beta^2 M X1
     T scale;                        // applied to the combined result
     const T *lift;                  // nullable: n_y vector; plane 0 gets -lift[i] * Mx[j]
+    const T *lift2y, *lift2x;       // nullable: plane p also gets -lift2y[i] * Mx[j] * lift2x[p][j] (n_x per plane)
     T *out;                         // packed mode planes [nz][n2]
     T *out1;                        // nullable: packed FFT of X1 alone
     T two_pi_over_lz;
@@ -674,6 +675,10 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
         if (p == 0 && a.lift) {
             const int i = qg / G.nx, j = qg % G.nx;
             v -= a.lift[i] * G.Mx[j];
+        }
+        if (a.lift2y) {
+            const int i = qg / G.nx, j = qg % G.nx;
+            v -= a.lift2y[i] * G.Mx[j] * a.lift2x[(long long)p * G.nx + j];
         }
         a.out[(long long)p * G.n2 + qg] = v;
         if (a.out1) a.out1[(long long)p * G.n2 + qg] = im ? X1.y : X1.x;
@@ -1627,6 +1632,77 @@ __global__ void __launch_bounds__(256) k_fdm_cluster(const float *__restrict__ r
                     C2[o] = u;
                 }
             }
+    }
+}
+
+// ---- electrode patches: capacitance correction of the potential (eq. 21) ----------------------
+// Plane p = blockIdx.x.  y: base solution with the whole wall Dirichlet at the values w[p][:]
+// (electrode voltages in plane 0, the previous gap values); rhs: its right-hand side, whose wall
+// row is b_G - Ky[0][0] Mx[j] w[j] (the forward transform's lifting).  For gap node j:
+//   s_j = b_G,j - (A_G,wall w)_j - (A_GI y)_j,
+//   (A_G,wall w)_j = My[0] sum_l Kx[j][l] w[l] + Mx[j] (Ky[0][0] + c_p My[0]) w[j],
+//   (A_GI y)_j = Mx[j] sum_{i >= 1} Ky[0][i] y[i][j];
+// the Ky[0][0] part is already in rhs.
+// d = Cinv_p s (m x m), and the right-hand side of the correction solve
+// rhs2[i][j] = Ky[i][0] Mx[j] d_j on gap columns (i >= 1), 0 elsewhere.
+template <typename T>
+__global__ void k_cap_solve(Geo<T> G, const T *__restrict__ rhs, const T *__restrict__ y, const int *__restrict__ gapj,
+                            const int *__restrict__ gapidx, int m, const T *__restrict__ w,
+                            const T *__restrict__ Kx, const T *__restrict__ Ky0, T my0,
+                            const T *__restrict__ sh, const T *__restrict__ Cinv, T *__restrict__ d,
+                            T *__restrict__ rhs2) {
+    extern __shared__ unsigned char pf_smem_raw[];
+    T *s = reinterpret_cast<T *>(pf_smem_raw);
+    T *ds = s + m;
+    const int p = blockIdx.x, nx = G.nx, ny = G.ny;
+    const long long base = (long long)p * G.n2;
+    const T *wp = w + (long long)p * nx;
+    const T c = sh[p];
+    const int imax = min(G.K, ny - 1);   // K_y[0][i] vanishes beyond the first element
+    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+        const int j = gapj[jj];
+        T acc = 0;
+        for (int i = 1; i <= imax; ++i) acc += Ky0[i] * y[base + (long long)i * nx + j];
+        T kw = 0;
+        for (int l = 0; l < nx; ++l) kw += Kx[(long long)j * nx + l] * wp[l];
+        s[jj] = rhs[base + j] - G.Mx[j] * acc - my0 * kw - G.Mx[j] * c * my0 * wp[j];
+    }
+    __syncthreads();
+    const T *Ci = Cinv + (long long)p * m * m;
+    for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+        T acc = 0;
+        for (int ll = 0; ll < m; ++ll) acc += Ci[(long long)jj * m + ll] * s[ll];
+        ds[jj] = acc;
+        d[(long long)p * m + jj] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < G.n2; q += blockDim.x) {
+        const int i = q / nx, j = q - (q / nx) * nx;
+        const int jj = gapidx[j];
+        rhs2[base + q] = (i >= 1 && jj >= 0) ? Ky0[i] * G.Mx[j] * ds[jj] : T(0);
+    }
+}
+
+// V = y - z off the wall (z nullable: no gap nodes); on the wall w + d (d on gaps only), and w
+// takes the new gap values
+template <typename T>
+__global__ void k_cap_combine(Geo<T> G, const T *y, const T *z, const T *__restrict__ d, const int *__restrict__ gapidx,
+                              int m, T *__restrict__ w, T *out, long long total) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long p = t / G.n2;
+        const int q = (int)(t - p * G.n2), i = q / G.nx, j = q - (q / G.nx) * G.nx;
+        if (i > 0) {
+            out[t] = z ? y[t] - z[t] : y[t];
+        } else {
+            const int jj = gapidx[j];
+            T v = w[p * G.nx + j];
+            if (jj >= 0) {
+                v += d[p * m + jj];
+                w[p * G.nx + j] = v;
+            }
+            out[t] = v;
+        }
     }
 }
 

@@ -18,7 +18,7 @@ from . import _build
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENOTSEPARABLE, PF_EDIVERGED, PF_ETIMEOUT, PF_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
-PF_BC_DIRICHLET, PF_BC_NEUMANN = 0, 1
+PF_BC_DIRICHLET, PF_BC_NEUMANN, PF_BC_PATCHES = 0, 1, 2
 PF_FP64, PF_MIXED, PF_MIXED_SIMT = 0, 1, 2
 PF_BCSET_V, PF_BCSET_NN, PF_BCSET_P, PF_BCSET_U = 0, 1, 2, 3
 PF_MODEL_FULL, PF_MODEL_EQUILIBRIUM = 0, 1
@@ -49,7 +49,9 @@ class PfFluid(ctypes.Structure):
 
 
 class PfVbc(ctypes.Structure):
-    _fields_ = [("bottom_kind", c_int), ("top_kind", c_int), ("v_bottom", c_double), ("v_top", c_double)]
+    _fields_ = [("bottom_kind", c_int), ("top_kind", c_int), ("v_bottom", c_double), ("v_top", c_double),
+                ("n_patch", c_int), ("patch_x0", POINTER(c_double)), ("patch_x1", POINTER(c_double)),
+                ("patch_v", POINTER(c_double))]
 
 
 class PfScheme(ctypes.Structure):
@@ -201,8 +203,10 @@ class Solver:
         self.mesh = PfMesh(len(self._xb) - 1, len(self._yb) - 1, _dp(self._xb), _dp(self._yb), int(order),
                            int(nz), float(lz))
         self.fluid = PfFluid(**{k: float(v) for k, v in fluid.items()})
+        pats = tuple(vbc.get("patches", ()))
+        self._patch = [_f64([p[c] for p in pats]) for c in range(3)]   # kept alive for pf_create
         self.vbc = PfVbc(int(vbc["bottom_kind"]), int(vbc["top_kind"]), float(vbc["v_bottom"]),
-                         float(vbc["v_top"]))
+                         float(vbc["v_top"]), len(pats), *(_dp(a) for a in self._patch))
         self.scheme = PfScheme(float(scheme["dt"]), int(scheme.get("bdf", 2)), int(scheme.get("precision", PF_FP64)),
                                float(scheme.get("S", 0.0)), float(scheme.get("nu_m", 0.0)),
                                float(scheme.get("rho0", 0.0)), float(scheme.get("eps0", 0.0)),
@@ -316,7 +320,8 @@ def from_workload(wl, precision: int = PF_FP64, stream: Optional[int] = None, dt
         phi0 = workloads.eval_on_grid(wl.phi0, x, y, z)
     fluid = dict(rho1=f.rho1, rho2=f.rho2, mu1=f.mu1, mu2=f.mu2, eps1=f.eps1, eps2=f.eps2, sigma=f.sigma,
                  eta=f.eta, gamma1=f.gamma1, theta_s_deg=f.theta_s_deg)
-    vbc = dict(bottom_kind=v.bottom_kind, top_kind=v.top_kind, v_bottom=v.v_bottom, v_top=v.v_top)
+    vbc = dict(bottom_kind=v.bottom_kind, top_kind=v.top_kind, v_bottom=v.v_bottom, v_top=v.v_top,
+               patches=tuple(getattr(v, "patches", ())))
     scheme = dict(dt=s.dt if dt is None else dt, bdf=s.bdf, precision=precision, S=s.S, nu_m=s.nu_m,
                   rho0=s.rho0, eps0=s.eps0,
                   model=PF_MODEL_EQUILIBRIUM if getattr(s, "equilibrium", False) else PF_MODEL_FULL)

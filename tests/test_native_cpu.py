@@ -8,6 +8,8 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
+import workloads
+
 from oracle.gll import gll as oracle_gll
 from oracle.sem import Mesh2D
 from paper_2305_09020_gb300 import native
@@ -133,7 +135,14 @@ def _create(**over):
     fluid = native.PfFluid(**fl)
     vb = dict(bottom_kind=0, top_kind=0, v_bottom=1.0, v_top=0.0)
     vb.update({k: v for k, v in over.items() if k in vb})
-    vbc = native.PfVbc(**vb)
+    pats = over.get("patches")
+    if pats is not None:
+        arrs = [np.ascontiguousarray([p[c] for p in pats], dtype=np.float64) for c in range(3)]
+        null = over.get("null_patch", False)
+        vbc = native.PfVbc(**vb, n_patch=over.get("n_patch", len(pats)),
+                           **{n: (None if null else native._dp(a)) for n, a in zip(("patch_x0", "patch_x1", "patch_v"), arrs)})
+    else:
+        vbc = native.PfVbc(**vb)
     sc = dict(dt=1e-3, bdf=2, precision=0, model=0)
     sc.update({k: v for k, v in over.items() if k in sc})
     scheme = native.PfScheme(sc["dt"], sc["bdf"], sc["precision"], 0.0, 0.0, 0.0, 0.0, sc.get("model", 0))
@@ -150,6 +159,12 @@ def _create(**over):
     (dict(bottom_kind=1, top_kind=1), "electrode"), (dict(bottom_kind=7), "bottom_kind"),
     (dict(dt=-1.0), "dt"), (dict(bdf=3), "bdf"), (dict(precision=9), "precision"),
     (dict(eta=0.0), "positive"), (dict(model=5), "model"), (dict(rho2=-1.0), "positive"), (dict(null_phi=True), "null"),
+    (dict(bottom_kind=2, patches=[(0.1, 0.2, 1.0)], n_patch=-1), "patch"),
+    (dict(bottom_kind=2, patches=[(0.1, 0.2, 1.0)], null_patch=True), "patch"),
+    (dict(bottom_kind=2, patches=[(0.3, 0.2, 1.0)]), "x0 <= x1"),
+    (dict(bottom_kind=2, patches=[(0.1, float("nan"), 1.0)]), "finite"),
+    (dict(top_kind=2), "top_kind"),
+    (dict(bottom_kind=2, top_kind=1, patches=[(0.3, 0.3, 1.0)]), "undetermined"),
 ])
 def test_create_rejects_bad_descriptors_without_gpu(over, needle):
     rc, msg, h = _create(**over)
@@ -163,3 +178,26 @@ def test_null_handles_are_rejected():
     assert L.pf_sync(None) == native.PF_EINVAL
     assert L.pf_diagnostics(None, None) == native.PF_EINVAL
     L.pf_destroy(None)          # no-op
+
+
+def test_ensembles_reject_electrode_patches_without_gpu():
+    """Ensembles take whole-side conditions only; the check happens before any CUDA call."""
+    import ctypes
+    L = native.load()
+    wl = workloads.patches2d(ex=4, ey=2, order=4)
+    m = wl.mesh
+    xb, yb = np.ascontiguousarray(m.xb), np.ascontiguousarray(m.yb)
+    mesh = (native.PfMesh * 1)(native.PfMesh(m.ex if hasattr(m, "ex") else len(xb) - 1, len(yb) - 1,
+                                             native._dp(xb), native._dp(yb), m.order, 1, 1.0))
+    f = wl.fluid
+    fluid = (native.PfFluid * 1)(native.PfFluid(f.rho1, f.rho2, f.mu1, f.mu2, f.eps1, f.eps2, f.sigma, f.eta,
+                                                f.gamma1, f.theta_s_deg))
+    arrs = [np.ascontiguousarray([p[c] for p in wl.vbc.patches]) for c in range(3)]
+    vbc = (native.PfVbc * 1)(native.PfVbc(2, 1, 0.0, 0.0, len(wl.vbc.patches), *(native._dp(a) for a in arrs)))
+    scheme = native.PfScheme(1e-4, 2, 0, 0.0, 0.0, 0.0, 0.0, 0)
+    phi = np.zeros(len(xb) * len(yb) * m.order * m.order)
+    phis = (ctypes.POINTER(ctypes.c_double) * 1)(native._dp(phi))
+    h = ctypes.c_void_p()
+    rc = L.pf_batch_create(1, mesh, fluid, vbc, ctypes.byref(scheme), phis, None, ctypes.byref(h))
+    assert rc == native.PF_EINVAL and h.value is None
+    assert "patch" in L.pf_last_error(None).decode()
