@@ -41,17 +41,34 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# ---- workloads that bench.py can time ------------------------------------------------------------
+WORKLOADS = {
+    "droplet3d": "droplet3d: 16x8 elements order 8 x Nz=64 planes, sphere r=0.25 on the electrode, "
+                 "eps/rho/mu ratios 10/2/5, V=2, dt=5e-5",
+    "electrode_array3d": "electrode_array3d: 20x6 elements order 12 x Nz=120 planes, ten electrode stripes "
+                         "at +-150 V (the paper's normalisation), hemispherical drop, permittivity ratio 32, "
+                         "equilibrium system, pseudo-time step 2e-6",
+    "patches2d": "patches2d: 16x4 elements order 8, four electrodes at -+0.5 on the wall, half-disc drop, "
+                 "eps/rho/mu ratios 5/2/2, dt=1e-4",
+}
+
+
+def make_workload(name):
+    import workloads
+    return getattr(workloads, name)()
+
+
 # ---- CPU oracle sample (cpu_baseline and --impl reference) -----------------------------------
-def oracle_sample(nsteps: int, warmup: int):
+def oracle_sample(nsteps: int, warmup: int, name: str = "droplet3d"):
     """Steady-state BDF2 steps of the FP64 oracle on the workload's element mesh and physics
-    with Nz = 8 planes (the oracle's sparse LU factorisations per mode make the full Nz = 64
-    case take minutes per step).  Returns (DOF-steps/s, seconds, description)."""
+    (3D: with Nz = 8 planes; the oracle's sparse LU factorisations per mode make the full plane
+    counts take minutes per step).  Returns (DOF-steps/s, seconds, description)."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import numpy as np
-    import workloads
     from oracle.runner import solver_of
-    wl = workloads.droplet3d()
-    wl.mesh.nz = 8
+    wl = make_workload(name)
+    if wl.mesh.nz > 1:
+        wl.mesh.nz = 8
     sol = solver_of(wl, init=False)
     Zg, Yg, Xg = np.meshgrid(sol.zc, sol.mesh.Y, sol.mesh.X, indexing="ij")
     sol.set_initial(wl.phi0(Xg, Yg, Zg).reshape(sol.nz, sol.mesh.n2), max_iter=3)
@@ -62,8 +79,9 @@ def oracle_sample(nsteps: int, warmup: int):
         sol.step()
     dt = time.perf_counter() - t0
     dof = sol.mesh.n2 * sol.nz
-    desc = (f"oracle (scipy SuperLU, numpy FFT), droplet3d element mesh 16x8 P=8 with Nz=8 planes "
-            f"({dof} DOF), {nsteps} steady BDF2 step(s) after {max(2, warmup)} warm-up steps; "
+    desc = (f"oracle (scipy SuperLU, numpy FFT), {name} element mesh"
+            + (" with Nz=8 planes" if sol.nz > 1 else "") +
+            f" ({dof} DOF), {nsteps} steady BDF2 step(s) after {max(2, warmup)} warm-up steps; "
             f"initial-potential iterations capped at 3 (set-up is not timed)")
     return dof * nsteps / dt, dt, desc
 
@@ -73,11 +91,12 @@ def reference_arm(args):
     if rank != 0:
         return 0
     steps = max(1, args.steps)
-    val, secs, desc = oracle_sample(steps, args.warmup)
+    val, secs, desc = oracle_sample(steps, args.warmup, args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "droplet3d (oracle sample: Nz=8)"},
+            "data": "synthetic", "config": {"workload": f"{args.workload} (oracle sample" +
+                                                        (": Nz=8)" if args.workload != "patches2d" else ")")},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -142,12 +161,13 @@ def transform_bytes_per_launch(nx, ny, nz, prec):
     return w * (2 * nx * ny * nz + max(nx, ny) ** 2)
 
 
-def fdm_flops_per_step(nx, ny, nz, d3):
+def fdm_flops_per_step(nx, ny, nz, d3, equilibrium=False, patches=False):
     """Fast-diagonalisation flops of one step: 4 n2 (n_x + n_y) per real plane and solve
-    (two GEMM passes each way); planes: V, psi, phi, P (Nz each) and d velocity components."""
+    (two GEMM passes each way); solves: V, psi, phi, P and d velocity components (the
+    equilibrium system: V, psi, phi), and with electrode patches a second V solve."""
     n2 = nx * ny
-    planes = nz * (4 + (3 if d3 else 2))
-    return 4.0 * n2 * (nx + ny) * planes
+    solves = (3 if equilibrium else 4 + (3 if d3 else 2)) + (1 if patches else 0)
+    return 4.0 * n2 * (nx + ny) * nz * solves
 
 
 def warmstart_arm(args):
@@ -191,6 +211,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
+    ap.add_argument("--workload", default="droplet3d", choices=sorted(WORKLOADS),
+                    help="droplet3d (the default bench line), or the electrode workloads")
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the transform variant (a PF_GEMM_* code) instead of autotuning")
@@ -225,7 +247,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prec = {"mixed": native.PF_MIXED, "mixed_simt": native.PF_MIXED_SIMT, "fp64": native.PF_FP64}[args.precision]
-    wl = workloads.droplet3d()
+    wl = make_workload(args.workload)
     m = wl.mesh
     nx, ny, nz = m.ex * m.order, m.ey * m.order + 1, m.nz
     dof = nx * ny * nz
@@ -285,7 +307,8 @@ def main():
         per_launch_ms = cls[top][0] / max(1, cls[top][1] - launches1[top][1])
         roof = None
         if top == "gemm":
-            flops = fdm_flops_per_step(nx, ny, nz, nz > 1) * args.steps
+            flops = fdm_flops_per_step(nx, ny, nz, nz > 1, bool(getattr(wl.scheme, "equilibrium", False)),
+                                       wl.vbc.bottom_kind == workloads.BC_PATCHES) * args.steps
             nlaunch = cls["gemm"][1] - launches1["gemm"][1]
             achieved = flops / nlaunch / (per_launch_ms * 1e-3) / 1e12
             if prec == native.PF_MIXED and gemm_choice == 0:
@@ -302,7 +325,8 @@ def main():
                 peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
                 roof = {"bound": "alu", "kernel": transform_kernel(gemm_choice, fused_y) + " (FP64 SIMT transforms)",
                         "peak_source": f"derived: {SM_COUNT} SMs x 2 FP64 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
-            traffic = TRANSFORM_DRAM_BYTES_PER_LAUNCH.get((args.precision, gemm_choice, fused_y))
+            traffic = (TRANSFORM_DRAM_BYTES_PER_LAUNCH.get((args.precision, gemm_choice, fused_y))
+                       if args.workload == "droplet3d" else None)
             roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "traffic_note": None if traffic is None else
@@ -337,7 +361,7 @@ def main():
                          "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes),
                          "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,phi,P,u), pinned host buffers"}
         if rank == 0 and world == 1:
-            val, secs, desc = oracle_sample(1, 2)
+            val, secs, desc = oracle_sample(1, 2, args.workload)
             extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     h.close()
 
@@ -345,8 +369,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == native.PF_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": "droplet3d: 16x8 elements order 8 x Nz=64 planes, sphere r=0.25 on the "
-                                   "electrode, eps/rho/mu ratios 10/2/5, V=2, dt=5e-5",
+            "config": {"workload": WORKLOADS[args.workload],
                        "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                        "fdm_gemm": {0: "tcgen05 3xTF32", 1: "whole solve per plane in shared memory (SIMT)",

@@ -81,7 +81,7 @@ typedef struct {
     const double *xb;      /* ex+1 increasing breakpoints in x (period xb[ex]-xb[0])       */
     const double *yb;      /* ey+1 increasing breakpoints in y (graded meshes allowed)     */
     int order;             /* element order K (K+1 GLL nodes per direction), 2 <= K <= 15  */
-    int nz;                /* Fourier planes in z: 1 (2D) or an even power of two <= 1024  */
+    int nz;                /* Fourier planes in z: 1 (2D) or an even 2^a 3^b 5^c 7^d <= 1024 */
     double lz;             /* period in z (ignored when nz == 1)                           */
 } pf_mesh;
 

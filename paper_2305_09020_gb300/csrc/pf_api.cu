@@ -487,8 +487,11 @@ struct Engine {
     }
     dim3 elem_grid() const { return dim3((ex * ey + epb() - 1) / epb(), nz); }
     // pencils per transform block: enough blocks for 4 per SM, shared memory <= 24 KiB
+    // transform buffers of a non-power-of-two nz need a second (scratch) copy for the mixed radices
+    bool nz_pow2() const { return (nz & (nz - 1)) == 0; }
+    size_t fft_scratch(int pencils) const { return nz_pow2() ? 0 : (size_t)pencils * (nz + 1) * sizeof(cplx<T>); }
     int fwd_tp() const {
-        int tp = (int)(24576 / (sizeof(cplx<T>) * (nz + 1)));
+        int tp = (int)((nz_pow2() ? 24576 : 12288) / (sizeof(cplx<T>) * (nz + 1)));
         const int by_grid = tp_override > 0 ? tp_override : n2 / (4 * 152);
         if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;
@@ -685,7 +688,8 @@ struct Engine {
         a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int) +
+                            fft_scratch(a.tp);
         prof->begin(PF_KC_FWD, st);
         pf::k_fwd<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
         check_launch();
@@ -698,7 +702,7 @@ struct Engine {
         a.Y = Y; a.phi_variant = 0; a.drow0 = drow0; a.drow1 = drow1; a.v0 = (T)v0; a.v1 = (T)v1;
         a.out = out; a.dzout = d3 ? dzout : nullptr; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(a.tp);
         prof->begin(PF_KC_INV, st);
         pf::k_inv<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
         check_launch();
@@ -712,7 +716,7 @@ struct Engine {
         a.out = phi_out; a.dzout = d3 ? dzphi_out : nullptr; a.out2 = W; a.dzout2 = d3 ? dzW : nullptr;
         a.out3 = Lf; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz); a.tw = tw;
         a.tp = std::max(4, fwd_tp() / 2);    // still a power of two
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(2 * a.tp);
         prof->begin(PF_KC_INV, st);
         pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
         check_launch();
@@ -821,7 +825,7 @@ struct Engine {
             faceh = FACEH;
         } else if (q.wetting) {
             const int tp = fwd_tp();
-            const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + tp * (nz + 1)) * sizeof(cplx<T>);
+            const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(tp);
             prof->begin(PF_KC_OTHER, st);
             pf::k_face_fft<T><<<(nx + tp - 1) / tp, 256, smem, st>>>(G, faceU, FACEH, tw, tp);
             check_launch();
@@ -1204,8 +1208,13 @@ int fill_setup(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc, co
     if (!mesh || !fluid || !vbc || !scheme) return bad("null argument");
     if (mesh->ex < 1 || mesh->ey < 1 || !mesh->xb || !mesh->yb) return bad("bad element counts");
     if (mesh->order < 2 || mesh->order > 15) return bad("order must be in [2, 15]");
-    if (mesh->nz < 1 || (mesh->nz > 1 && ((mesh->nz & (mesh->nz - 1)) != 0 || mesh->nz > 1024)))
-        return bad("nz must be 1 or a power of two <= 1024");
+    if (mesh->nz < 1 || mesh->nz > 1024) return bad("nz must be 1 or an even product of 2, 3, 5, 7 <= 1024");
+    if (mesh->nz > 1) {
+        int r = mesh->nz;
+        for (int f : {2, 3, 5, 7})
+            while (r % f == 0) r /= f;
+        if (r != 1 || mesh->nz % 2 != 0) return bad("nz must be 1 or an even product of 2, 3, 5, 7 <= 1024");
+    }
     if (mesh->nz > 1 && !(mesh->lz > 0)) return bad("lz must be positive");
     if (mesh->ex * mesh->order < 2) return bad("need at least 2 nodes in x");
     for (int e = 0; e < mesh->ex; ++e)

@@ -538,6 +538,71 @@ __device__ void fft_pencils(cplx<T> *buf, int ld, int npen, int n, const cplx<T>
     }
 }
 
+// Stockham autosort FFT of npen pencils of any even length n = 2^a 3^b 5^c 7^d (natural order in
+// and out; the result ends in buf, tmp is scratch of the same shape).  Each stage of radix R
+// (4, 2, 3, 5 or 7, taken in that order while it divides what is left) combines R inputs
+// x[j + r n/R] of the pencil, twiddled by w^(r (j mod Ns) n/(Ns R)), through an R-point DFT into
+// the outputs (j / Ns) Ns R + (j mod Ns) + s Ns, Ns = product of the earlier radices.  Twiddles
+// w^m = exp(-+2 pi i m / n) come from the half table tw (w^(m + n/2) = -w^m).
+template <typename T>
+__device__ void fft_pencils_mixed(cplx<T> *buf, cplx<T> *tmp, int ld, int npen, int n, const cplx<T> *tw,
+                                  bool inverse) {
+    const int h = n / 2;
+    auto W = [&](int m) {
+        cplx<T> w = m < h ? tw[m] : cplx<T>{-tw[m - h].x, -tw[m - h].y};
+        if (inverse) w.y = -w.y;
+        return w;
+    };
+    cplx<T> *in = buf, *out = tmp;
+    int Ns = 1, rem = n;
+    while (rem > 1) {
+        const int R = (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : (rem % 3 == 0) ? 3 : (rem % 5 == 0) ? 5 : 7;
+        const int nb = n / R, tstep = n / (Ns * R), sstep = n / R;
+        for (int t = threadIdx.x; t < npen * nb; t += blockDim.x) {
+            const int pen = t / nb, j = t - pen * nb, k = j % Ns;
+            const cplx<T> *x = in + pen * ld;
+            cplx<T> *y = out + pen * ld;
+            cplx<T> v[7];
+#pragma unroll
+            for (int r = 0; r < 7; ++r) {
+                if (r >= R) break;
+                v[r] = x[j + r * nb];
+                if (r) v[r] = cmul(v[r], W(r * k * tstep));
+            }
+            const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int s = 0; s < 7; ++s) {
+                if (s >= R) break;
+                cplx<T> acc = v[0];
+#pragma unroll
+                for (int r = 1; r < 7; ++r) {
+                    if (r >= R) break;
+                    const cplx<T> p = cmul(v[r], W(((r * s) % R) * sstep));
+                    acc.x += p.x;
+                    acc.y += p.y;
+                }
+                y[o + s * Ns] = acc;
+            }
+        }
+        __syncthreads();
+        cplx<T> *sw = in;
+        in = out;
+        out = sw;
+        Ns *= R;
+        rem /= R;
+    }
+    if (in != buf) {
+        for (int t = threadIdx.x; t < npen * n; t += blockDim.x) {
+            const int pen = t / n, i = t - pen * n;
+            buf[pen * ld + i] = in[pen * ld + i];
+        }
+        __syncthreads();
+    }
+}
+
+// position of sample (or mode) i in the transform buffer: bit-reversed for the radix-2 DIT
+__device__ __forceinline__ int fft_slot(int i, int bits, bool pow2) { return pow2 ? bitrev(i, bits) : i; }
+
 // mode index k and real/imaginary part of packed plane p
 __device__ __forceinline__ void plane_mode(int p, int nz, int &k, int &im) {
     if (nz == 1 || p == 0) { k = 0; im = 0; return; }
@@ -606,6 +671,8 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     const int nz = G.nz, ld = nz + 1, tp = a.tp;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
     int *ssrc = reinterpret_cast<int *>(buf + tp * ld);   // tp x 4 DSSUM sources
+    const bool pow2 = (nz & (nz - 1)) == 0;
+    cplx<T> *tmp = reinterpret_cast<cplx<T> *>(ssrc + tp * 4);   // mixed-radix scratch (nz not 2^k)
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
     const int q0 = blockIdx.x * tp;
@@ -640,12 +707,15 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
             const int idx = base + u * blockDim.x;
             if (idx < total) {
                 const int z = idx >> lgtp, ql = idx & (tp - 1);
-                buf[ql * ld + bitrev(z, bits)] = {v0[u], v1[u]};
+                buf[ql * ld + fft_slot(z, bits, pow2)] = {v0[u], v1[u]};
             }
         }
     }
     __syncthreads();
-    if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
+    if (nz > 1) {
+        if (pow2) fft_pencils(buf, ld, tp, nz, stw, false);
+        else fft_pencils_mixed(buf, tmp, ld, tp, nz, stw, false);
+    }
     const T inv_n = T(1) / T(nz);
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
         const int p = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
@@ -707,12 +777,12 @@ struct InvArgs {
 // Build the full complex spectrum Z = X + i Y of two real signals, Y = i beta X (d/dz),
 // from the packed half spectrum X of pencil column ql; buffer is bit-reversed for the DIT.
 template <typename T>
-__device__ __forceinline__ void put_pair(cplx<T> *x, int nz, int bits, int k, cplx<T> Xk, T beta) {
+__device__ __forceinline__ void put_pair(cplx<T> *x, int nz, int bits, bool pow2, int k, cplx<T> Xk, T beta) {
     // Z_k = (1 - beta) X_k ; Z_{N-k} = (1 + beta) conj(X_k)
     const bool nyq = (nz > 1 && k == nz / 2);
     const T b = nyq ? T(0) : beta;
-    x[bitrev(k, bits)] = {(T(1) - b) * Xk.x, (T(1) - b) * Xk.y};
-    if (k != 0 && !nyq) x[bitrev(nz - k, bits)] = {(T(1) + b) * Xk.x, -(T(1) + b) * Xk.y};
+    x[fft_slot(k, bits, pow2)] = {(T(1) - b) * Xk.x, (T(1) - b) * Xk.y};
+    if (k != 0 && !nyq) x[fft_slot(nz - k, bits, pow2)] = {(T(1) + b) * Xk.x, -(T(1) + b) * Xk.y};
 }
 
 template <typename T>
@@ -727,6 +797,8 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     const int nz = G.nz, ld = nz + 1, tp = a.tp;
     const int npair = a.phi_variant ? 2 : 1;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    const bool pow2 = (nz & (nz - 1)) == 0;
+    cplx<T> *tmp = buf + tp * npair * ld;   // mixed-radix scratch (nz not 2^k)
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
     const int q0 = blockIdx.x * tp;
@@ -759,12 +831,15 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
             buf[ql * ld] = X;
             if (a.phi_variant) buf[(tp + ql) * ld] = Wk;
         } else {
-            put_pair(buf + ql * ld, nz, bits, k, X, beta);
-            if (a.phi_variant) put_pair(buf + (tp + ql) * ld, nz, bits, k, Wk, beta);
+            put_pair(buf + ql * ld, nz, bits, pow2, k, X, beta);
+            if (a.phi_variant) put_pair(buf + (tp + ql) * ld, nz, bits, pow2, k, Wk, beta);
         }
     }
     __syncthreads();
-    if (nz > 1) fft_pencils(buf, ld, tp * npair, nz, stw, true);
+    if (nz > 1) {
+        if (pow2) fft_pencils(buf, ld, tp * npair, nz, stw, true);
+        else fft_pencils_mixed(buf, tmp, ld, tp * npair, nz, stw, true);
+    }
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
         const int z = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
         if (qg >= G.n2) continue;
@@ -898,6 +973,8 @@ __global__ void k_face_fft(Geo<T> G, const T *__restrict__ face, T *__restrict__
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
     const int nz = G.nz, ld = nz + 1;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
+    const bool pow2 = (nz & (nz - 1)) == 0;
+    cplx<T> *tmp = buf + tp * ld;   // mixed-radix scratch (nz not 2^k)
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = tw[i];
     const int j0 = blockIdx.x * tp;
@@ -914,10 +991,13 @@ __global__ void k_face_fft(Geo<T> G, const T *__restrict__ face, T *__restrict__
                 v = face[(base + j / K) * p + j % K];
             }
         }
-        buf[jl * ld + bitrev(z, bits)] = {v, T(0)};
+        buf[jl * ld + fft_slot(z, bits, pow2)] = {v, T(0)};
     }
     __syncthreads();
-    if (nz > 1) fft_pencils(buf, ld, tp, nz, stw, false);
+    if (nz > 1) {
+        if (pow2) fft_pencils(buf, ld, tp, nz, stw, false);
+        else fft_pencils_mixed(buf, tmp, ld, tp, nz, stw, false);
+    }
     const T inv_n = T(1) / T(nz);
     for (int idx = threadIdx.x; idx < tp * nz; idx += blockDim.x) {
         const int p = idx >> lgtp, jl = idx & (tp - 1), j = j0 + jl;

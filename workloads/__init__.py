@@ -251,6 +251,40 @@ def patches2d(ex: int = 16, ey: int = 4, order: int = 8, nz: int = 1, v0: float 
     )
 
 
+def electrode_array3d(ex: int = 20, ey: int = 6, order: int = 12, nz: int = 120, volts: float = 150.0,
+                      eta: float = 0.02, dt: float = 2e-6, grading: float = 1.0) -> Workload:
+    """The 3D electrode-array drop of Sec. 4, normalised as the paper's table for the equilibrium
+    system (lengths by L0 = 1.2 mm, V by V_d = 150 V, permittivities by L0 gamma / V_d^2 with
+    gamma = 3.857e-2 kg/s^2, so eps_air = 4.30e-3 and the liquid's 32 times that): domain
+    [0, 5/3] x [0, 2/3] x [0, 7/2], ten electrode stripes along z of width 1/12 spaced 1/12 apart
+    (on x in [i/6, i/6 + 1/12], +V0 and -V0 alternating, V0 = volts / 150), dV/dn = 0 on the gaps
+    and on the open top; a hemispherical liquid drop (fluid 1) of radius 1/2 centred on the wall at
+    (5/6, 0, 7/4); eta = 0.02, lambda gamma1 = 0.1, pseudo-time step 2e-6; the equilibrium system
+    of Sec. 2.4 (u = 0).  Mesh: 20 uniform elements in x, 6 in y (grading 1: uniform; g > 1:
+    each element g times the one below), order 12, Nz = 120 Fourier planes."""
+
+    def phi0(x, y, z):
+        r = np.sqrt((x - 5.0 / 6.0) ** 2 + y ** 2 + (z - 1.75) ** 2)
+        return _tanh_profile(0.5 - r, eta)
+
+    lam = 3.0 * 1.0 * eta / (2.0 * np.sqrt(2.0))          # lambda with the normalised gamma = 1
+    e_air = 8.854e-12 * 150.0 ** 2 / (1.2e-3 * 3.857e-2)
+    h = grading ** np.arange(ey)
+    yb = (2.0 / 3.0) * np.concatenate([[0.0], np.cumsum(h) / np.sum(h)])
+    v0 = volts / 150.0
+    pats = tuple((i / 6.0, i / 6.0 + 1.0 / 12.0, v0 if i % 2 == 0 else -v0) for i in range(10))
+    return Workload(
+        name=f"electrode_array3d_{ex}x{ey}_K{order}_nz{nz}",
+        mesh=Mesh(xb=np.linspace(0.0, 5.0 / 3.0, ex + 1), yb=yb, order=order, nz=nz, lz=3.5),
+        fluid=Fluid(rho1=1.0, rho2=1.0, mu1=1.0, mu2=1.0, eps1=32.0 * e_air, eps2=e_air,
+                    sigma=1.0, eta=eta, gamma1=0.1 / lam, theta_s_deg=90.0),
+        vbc=VoltageBC(BC_PATCHES, BC_NEUMANN, patches=pats),
+        scheme=Scheme(dt=dt, equilibrium=True),
+        steps=10,
+        phi0=phi0,
+    )
+
+
 @dataclasses.dataclass
 class EnsembleMember:
     ex: int
