@@ -151,7 +151,7 @@ def transform_kernel(code, fused_y):
 
 # DRAM traffic per launch of a transform kernel on droplet3d, from one ncu capture of an unchanged
 # kernel (profiles/k_gemm_cp_droplet3d.md): (precision, variant code, fused y) -> bytes
-TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("mixed", 4, 0): 2.24e6}
+TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("mixed", 3, 0): 2.24e6}
 
 
 def transform_bytes_per_launch(nx, ny, nz, prec):
