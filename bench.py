@@ -236,7 +236,7 @@ def main():
     import torch
     import torch.distributed as dist
     import workloads
-    from paper_2305_09020_gb300 import native
+    from paper_2305_09020_gb300 import native, replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -285,11 +285,9 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in ev)
     launches1 = h.profile_read()
     gpu_launches = sum(launches1[k][1] - launches0[k][1] for k in launches1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = dof * args.steps * world / (ms * 1e-3)
+    ms = replicas.max_over_ranks(ms, dev)                       # the slowest replica's time
+    units = replicas.gather_counts(dof * args.steps, dev)      # DOF-steps of every replica
+    value = replicas.job_rate(units, ms * 1e-3)
 
     extras = {}
     if not args.skip_extras:
