@@ -536,7 +536,19 @@ struct Engine {
             constexpr int VWE = 16 / (int)sizeof(T);
             const bool vec = Ncol % VWE == 0 && ((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0;
             prof->begin(PF_KC_GEMM, st);
-            if (simt_tile == 3) {
+            if (Ncol > 64 && Ncol <= 80 && (simt_tile == 3 || simt_tile == 4)) {
+                // one 80-wide column tile (e.g. the y transforms of n_y = 65) instead of a second,
+                // nearly empty 64- or 32-wide one
+                if (simt_tile == 3) {
+                    dim3 grid(1, (unsigned)((Mrows + 63) / 64));
+                    if (vec) pf::k_gemm_cp<T, 64, 80, BK, 4, 4, 4, true><<<grid, 320, 0, st>>>(g);
+                    else pf::k_gemm_cp<T, 64, 80, BK, 4, 4, 4, false><<<grid, 320, 0, st>>>(g);
+                } else {
+                    dim3 grid(1, (unsigned)((Mrows + 31) / 32));
+                    if (vec) pf::k_gemm_cp<T, 32, 80, BK, 2, 4, 4, true><<<grid, 320, 0, st>>>(g);
+                    else pf::k_gemm_cp<T, 32, 80, BK, 2, 4, 4, false><<<grid, 320, 0, st>>>(g);
+                }
+            } else if (simt_tile == 3) {
                 dim3 grid((Ncol + 63) / 64, (unsigned)((Mrows + 63) / 64));
                 if (vec) pf::k_gemm_cp<T, 64, 64, BK, 4, 4, 4, true><<<grid, 256, 0, st>>>(g);
                 else pf::k_gemm_cp<T, 64, 64, BK, 4, 4, 4, false><<<grid, 256, 0, st>>>(g);
