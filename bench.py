@@ -339,25 +339,27 @@ def main():
 
         # end to end through the C-ABI with host buffers: set phi, u from pinned host memory,
         # step, read V, phi, P, u back into pinned host memory
+        # The state fields phi, u go host -> device and back through one pinned buffer (the next
+        # step's input is the last step's output, no host-side copy); V, P come back into another.
         n_e2e = min(args.steps, 20)
-        hin = torch.empty(4 * dof, dtype=torch.float64, pin_memory=True).numpy()
-        hout = torch.empty(6 * dof, dtype=torch.float64, pin_memory=True).numpy()
-        mask_in = native.PF_FIELD_PHI | native.PF_FIELD_U
-        mask_out = native.PF_FIELD_V | native.PF_FIELD_PHI | native.PF_FIELD_P | native.PF_FIELD_U
-        h.get_into(mask_in, hin)
+        hio = torch.empty(4 * dof, dtype=torch.float64, pin_memory=True).numpy()
+        hvp = torch.empty(2 * dof, dtype=torch.float64, pin_memory=True).numpy()
+        mask_io = native.PF_FIELD_PHI | native.PF_FIELD_U
+        mask_vp = native.PF_FIELD_V | native.PF_FIELD_P
+        h.get_into(mask_io, hio)
         barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            h.set(mask_in, hin)
+            h.set(mask_io, hio)
             h.step(1)
-            h.get_into(mask_out, hout)
-            hin[:dof] = hout[dof:2 * dof]          # phi
-            hin[dof:] = hout[3 * dof:]             # u
+            h.get_into(mask_vp, hvp)
+            h.get_into(mask_io, hio)
         barrier()
         te = time.perf_counter() - t0
         extras["e2e"] = {"value": dof * n_e2e * world / te, "unit": UNIT,
-                         "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes),
-                         "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,phi,P,u), pinned host buffers"}
+                         "h2d_bytes_per_step": int(hio.nbytes), "d2h_bytes_per_step": int(hio.nbytes + hvp.nbytes),
+                         "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,P) + "
+                                                 "pf_get_fields(phi,u), pinned host buffers, no host-side copies"}
         if rank == 0 and world == 1:
             val, secs, desc = oracle_sample(1, 2, args.workload)
             extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}

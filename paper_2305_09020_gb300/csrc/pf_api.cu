@@ -1161,6 +1161,8 @@ void upload_field(Engine<T> &E, T *dst, const double *host) {
     E.prof->end(E.st);
 }
 
+// Asynchronous on the engine's stream: the next conversion into the scratch follows the copy in
+// stream order; the caller synchronises before it reads the host buffer.
 template <typename T>
 void download_field(Engine<T> &E, const T *src, double *host) {
     double *scratch = reinterpret_cast<double *>(E.W2);
@@ -1169,7 +1171,6 @@ void download_field(Engine<T> &E, const T *src, double *host) {
     PF_CU(cudaGetLastError());
     E.prof->end(E.st);
     PF_CU(cudaMemcpyAsync(host, scratch, E.N * sizeof(double), cudaMemcpyDeviceToHost, E.st));
-    PF_CU(cudaStreamSynchronize(E.st));
 }
 
 // z-derivative of a physical field through the engine's own transforms (forward then
@@ -1407,12 +1408,14 @@ int get_impl(pf_handle *h, Engine<T> &E, unsigned mask, double *out, size_t n) {
         std::vector<double> phi(E.N);
         download_field(E, E.phi[E.cur], phi.data());
         download_field(E, E.Lf, o);
+        PF_CU(cudaStreamSynchronize(E.st));
         const double al = alpha_of(h->hs, h->last_J);
         for (long long i = 0; i < E.N; ++i) o[i] += al * phi[i];
         o += E.N;
     }
     if (mask & PF_FIELD_P) put(E.P[l]);
     if (mask & PF_FIELD_U) { put(E.u[0][l]); put(E.u[1][l]); put(E.u[2][l]); }
+    PF_CU(cudaStreamSynchronize(E.st));
     return PF_OK;
 }
 

@@ -1111,13 +1111,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
         if (m >= g.Mrows) continue;
         const long long p = m / g.R;
         const int r = (int)(m - p * g.R);
+        const T lr = g.lamN ? g.lamR[r] : T(0), cp = g.lamN ? g.cpl[p % g.cpl_mod] : T(0);   // once per row
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int n = n0 + tx * TN + j;
             if (n >= g.N) continue;
             T v = acc[i][j];
             if (g.lamN) {
-                const T d = g.lamN[n] + g.lamR[r] + g.cpl[p % g.cpl_mod];
+                const T d = g.lamN[n] + lr + cp;
                 v = (d != T(0)) ? v / d : T(0);
             }
             if (g.store == 0) g.C[m * g.N + n] = v;
@@ -1239,13 +1240,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_cp(GemmArgs<T> g
         if (m >= g.Mrows) continue;
         const long long p = m / g.R;
         const int r = (int)(m - p * g.R);
+        const T lr = g.lamN ? g.lamR[r] : T(0), cp = g.lamN ? g.cpl[p % g.cpl_mod] : T(0);   // once per row
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int n = n0 + tx * TN + j;
             if (n >= g.N) continue;
             T v = acc[i][j];
             if (g.lamN) {
-                const T d = g.lamN[n] + g.lamR[r] + g.cpl[p % g.cpl_mod];
+                const T d = g.lamN[n] + lr + cp;
                 v = (d != T(0)) ? v / d : T(0);
             }
             if (g.store == 0) g.C[m * g.N + n] = v;
