@@ -487,6 +487,23 @@ struct Engine {
     }
     dim3 elem_grid() const { return dim3((ex * ey + epb() - 1) / epb(), nz); }
     // pencils per transform block: enough blocks for 4 per SM, shared memory <= 24 KiB
+    // log2(nz) for the transform kernels compiled for a fixed plane count (16..256), else 0
+    int lgz() const {
+        if (!nz_pow2() || nz < 16 || nz > 256) return 0;
+        int l = 0;
+        while ((1 << l) < nz) ++l;
+        return l;
+    }
+    void launch_inv(dim3 grid, size_t smem, const pf::InvArgs<T> &a) {
+        switch (lgz()) {
+            case 4: pf::k_inv<T, 4><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 5: pf::k_inv<T, 5><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 6: pf::k_inv<T, 6><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 7: pf::k_inv<T, 7><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 8: pf::k_inv<T, 8><<<grid, 256, smem, st>>>(geo(), a); break;
+            default: pf::k_inv<T, 0><<<grid, 256, smem, st>>>(geo(), a);
+        }
+    }
     // transform buffers of a non-power-of-two nz need a second (scratch) copy for the mixed radices
     bool nz_pow2() const { return (nz & (nz - 1)) == 0; }
     size_t fft_scratch(int pencils) const { return nz_pow2() ? 0 : (size_t)pencils * (nz + 1) * sizeof(cplx<T>); }
@@ -703,7 +720,15 @@ struct Engine {
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int) +
                             fft_scratch(a.tp);
         prof->begin(PF_KC_FWD, st);
-        pf::k_fwd<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
+        const dim3 grid((n2 + a.tp - 1) / a.tp, ncomp);
+        switch (lgz()) {
+            case 4: pf::k_fwd<T, 4><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 5: pf::k_fwd<T, 5><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 6: pf::k_fwd<T, 6><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 7: pf::k_fwd<T, 7><<<grid, 256, smem, st>>>(geo(), a); break;
+            case 8: pf::k_fwd<T, 8><<<grid, 256, smem, st>>>(geo(), a); break;
+            default: pf::k_fwd<T, 0><<<grid, 256, smem, st>>>(geo(), a);
+        }
         check_launch();
         prof->end(st);
     }
@@ -716,7 +741,7 @@ struct Engine {
         a.tw = tw; a.tp = fwd_tp();
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(a.tp);
         prof->begin(PF_KC_INV, st);
-        pf::k_inv<T><<<dim3((n2 + a.tp - 1) / a.tp, ncomp), 256, smem, st>>>(geo(), a);
+        launch_inv(dim3((n2 + a.tp - 1) / a.tp, ncomp), smem, a);
         check_launch();
         prof->end(st);
     }
@@ -730,7 +755,7 @@ struct Engine {
         a.tp = std::max(4, fwd_tp() / 2);    // still a power of two
         const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(2 * a.tp);
         prof->begin(PF_KC_INV, st);
-        pf::k_inv<T><<<(n2 + a.tp - 1) / a.tp, 256, smem, st>>>(geo(), a);
+        launch_inv(dim3((n2 + a.tp - 1) / a.tp), smem, a);
         check_launch();
         prof->end(st);
     }

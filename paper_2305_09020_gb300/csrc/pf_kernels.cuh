@@ -515,10 +515,11 @@ __device__ __forceinline__ int bitrev(int v, int bits) { return bits ? (int)(__b
 // all index arithmetic is shifts and masks (n, the spans and the pencil count are powers of two
 // or plain multiples)
 template <typename T>
-__device__ void fft_pencils(cplx<T> *buf, int ld, int npen, int n, const cplx<T> *tw, bool inverse) {
+__device__ __forceinline__ void fft_pencils(cplx<T> *buf, int ld, int npen, int n, const cplx<T> *tw, bool inverse) {
     const int lg = 31 - __clz(n);
     const int hb = lg - 1;                       // log2(n / 2)
     const int nb = npen << hb;
+#pragma unroll
     for (int s = 1; s <= lg; ++s) {
         const int hs = s - 1;                    // log2(half span)
         const int hmask = (1 << hs) - 1;
@@ -659,7 +660,9 @@ __device__ __forceinline__ T gather4(const T *__restrict__ L, long long zoff, co
     return v;
 }
 
-template <typename T>
+// LGZ > 0: Nz = 2^LGZ fixed at compile time (the FFT stages unroll, index arithmetic on Nz folds);
+// LGZ = 0: Nz from G (any supported value)
+template <typename T, int LGZ = 0>
 __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     if (blockIdx.y) {   // component blockIdx.y of a batched launch
         a.X0 += blockIdx.y * a.cs_x0;
@@ -668,7 +671,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
-    const int nz = G.nz, ld = nz + 1, tp = a.tp;
+    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = nz + 1, tp = a.tp;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
     int *ssrc = reinterpret_cast<int *>(buf + tp * ld);   // tp x 4 DSSUM sources
     const bool pow2 = (nz & (nz - 1)) == 0;
@@ -785,7 +788,7 @@ __device__ __forceinline__ void put_pair(cplx<T> *x, int nz, int bits, bool pow2
     if (k != 0 && !nyq) x[fft_slot(nz - k, bits, pow2)] = {(T(1) + b) * Xk.x, -(T(1) + b) * Xk.y};
 }
 
-template <typename T>
+template <typename T, int LGZ = 0>   // LGZ as for k_fwd
 __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     if (blockIdx.y) {
         a.Y += blockIdx.y * a.cs_y;
@@ -794,7 +797,7 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
-    const int nz = G.nz, ld = nz + 1, tp = a.tp;
+    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = nz + 1, tp = a.tp;
     const int npair = a.phi_variant ? 2 : 1;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
     const bool pow2 = (nz & (nz - 1)) == 0;
