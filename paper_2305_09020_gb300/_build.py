@@ -1,9 +1,10 @@
 """Compile the in-tree CUDA library ``libpf.so`` for sm_103a with nvcc (no cmake)."""
 from __future__ import annotations
 
+import hashlib
 import os
 import subprocess
-import hashlib
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
@@ -39,12 +40,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if fh.read().strip() == dig:
                 return LIB
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "-shared", "-o", tmp,
-           *[os.path.join(CSRC, f) for f in SOURCES]]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
+    with tempfile.TemporaryDirectory(prefix="pf_build_") as work:
+        # one nvcc per translation unit, all at once, then one link
+        objs, procs = [], []
+        for f in SOURCES:
+            obj = os.path.join(work, f + ".o")
+            cmd = [nvcc(), *flags, "-c", os.path.join(CSRC, f), "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append((cmd, subprocess.Popen(cmd)))
+            objs.append(obj)
+        for cmd, p in procs:
+            if p.wait() != 0:
+                raise subprocess.CalledProcessError(p.returncode, cmd)
+        subprocess.run([nvcc(), ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     with open(stamp, "w") as fh:
         fh.write(dig)
