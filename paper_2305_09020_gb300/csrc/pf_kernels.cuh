@@ -143,12 +143,14 @@ __device__ __forceinline__ void load_tables(const Geo<T> &G, T *sD, T *sDw, T *s
 template <typename T>
 __device__ __forceinline__ T ddx(const T *f, const T *sD, int p, int a, int b, T sc) {
     T s = 0;
+#pragma unroll
     for (int m = 0; m < p; ++m) s += sD[a * p + m] * f[b * p + m];
     return s * sc;
 }
 template <typename T>
 __device__ __forceinline__ T ddy(const T *f, const T *sD, int p, int a, int b, T sc) {
     T s = 0;
+#pragma unroll
     for (int m = 0; m < p; ++m) s += sD[b * p + m] * f[m * p + a];
     return s * sc;
 }
@@ -156,6 +158,7 @@ __device__ __forceinline__ T ddy(const T *f, const T *sD, int p, int a, int b, T
 template <typename T>
 __device__ __forceinline__ T wdx(const T *F, const T *sDw, const T *sw, int p, int a, int b, T hy2) {
     T s = 0;
+#pragma unroll
     for (int m = 0; m < p; ++m) s += sDw[m * p + a] * F[b * p + m];
     return s * hy2 * sw[b];
 }
@@ -167,6 +170,18 @@ __device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, i
 }
 
 // shared memory: D, Dw, w tables, then nfields element arrays per local element
+// The element order fixed at compile time (KC > 0; KC = 0 keeps the run's order): loops over the
+// K + 1 nodes of an element unroll and slot arithmetic folds.  epb follows the host's choice.
+template <int KC, typename T>
+__device__ __forceinline__ Geo<T> fixed_order(Geo<T> g) {
+    if constexpr (KC > 0) {
+        g.K = KC;
+        g.p = KC + 1;
+        g.epb = 256 / ((KC + 1) * (KC + 1)) > 1 ? 256 / ((KC + 1) * (KC + 1)) : 1;
+    }
+    return g;
+}
+
 #define PF_ELEM_SMEM(T, G, nfields)                                                   \
     extern __shared__ unsigned char pf_smem_raw[];                                    \
     T *sD = reinterpret_cast<T *>(pf_smem_raw);                                       \
@@ -179,10 +194,11 @@ __device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, i
 // ---- eq. 54a / 74a: RHS of the potential --------------------------------------------------
 // A = -int R_2D . grad_2D w  (element-local contributions),  B = int R_z w  (iB multiplier)
 // with R = (eps(phi*) - eps0) grad V*.
-template <typename T>
-__global__ void k_potential(Geo<T> G, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
+template <typename T, int KC = 0>
+__global__ void k_potential(Geo<T> G_, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
                             const T *__restrict__ Vn, const T *__restrict__ Vo, const T *__restrict__ Ezn,
                             const T *__restrict__ Ezo, T *__restrict__ A, T *__restrict__ B) {
+    const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 3)
     const Phys<T> q = plane_phys(q_);
     T *sV = sF, *sRx = sF + pp_, *sRy = sF + 2 * pp_;
@@ -215,8 +231,9 @@ __global__ void k_potential(Geo<T> G, Phys<T> q_, const T *__restrict__ phin, co
 
 // ---- eq. 55 / 78: E_x, E_y = M^{-1} * sum over elements of M_e * (element derivative of V)
 // On a tensor mesh the y (resp. x) factors of M_e cancel, leaving a 1D weighted average.
-template <typename T>
-__global__ void k_efield(Geo<T> G, const T *__restrict__ V, T *__restrict__ Ex, T *__restrict__ Ey) {
+template <typename T, int KC = 0>
+__global__ void k_efield(Geo<T> G_, const T *__restrict__ V, T *__restrict__ Ex, T *__restrict__ Ey) {
+    const Geo<T> G = fixed_order<KC>(G_);
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tot = (long long)G.n2 * G.nz;
     if (gid >= tot) return;
@@ -269,13 +286,14 @@ __global__ void k_efield(Geo<T> G, const T *__restrict__ V, T *__restrict__ Ex, 
 // Q2 = h(phi*) - (S/eta^2) phi* - eps'(phi*)/(2 lambda) |E|^2 (nodal, written to Q2n),
 // A = -int Q1 w + int grad_2D Q2 . grad_2D w + (alpha + S/eta^2) int_wall U w,
 // U = -Theta'(phi*)/lambda; faceU (optional) = int_wall U w (element-local face slots).
-template <typename T>
-__global__ void k_chem(Geo<T> G, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
+template <typename T, int KC = 0>
+__global__ void k_chem(Geo<T> G_, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
                        const T *__restrict__ dzphin, const T *__restrict__ dzphio,
                        const T *__restrict__ uxn, const T *__restrict__ uxo, const T *__restrict__ uyn,
                        const T *__restrict__ uyo, const T *__restrict__ uzn, const T *__restrict__ uzo,
                        const T *__restrict__ Ex, const T *__restrict__ Ey, const T *__restrict__ Ez,
                        T *__restrict__ A, T *__restrict__ Q2n, T *__restrict__ faceU) {
+    const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 4)
     const Phys<T> q = plane_phys(q_);
     T *sP = sF, *sQ = sF + pp_, *sQx = sF + 2 * pp_, *sQy = sF + 3 * pp_;
@@ -336,8 +354,9 @@ struct MomOut {
     T *AP, *BP, *AU[3], *BU[3];
 };
 
-template <typename T>
-__global__ void k_momentum(Geo<T> G, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
+template <typename T, int KC = 0>
+__global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
+    const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 12)
     const Phys<T> q = plane_phys(q_);
     // inputs with in-plane derivatives: phi, W, u*_x, u*_y, u*_z, P*
@@ -463,9 +482,10 @@ __global__ void k_momentum(Geo<T> G, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
 }
 
 // -(1/(nu_m rho0)) int grad P^{n+1} v: added to AU[0], AU[1]; the z part is -(1/(nu_m rho0)) i beta int P v.
-template <typename T>
-__global__ void k_ugradp(Geo<T> G, Phys<T> q, const T *__restrict__ P, T *__restrict__ AUx,
+template <typename T, int KC = 0>
+__global__ void k_ugradp(Geo<T> G_, Phys<T> q, const T *__restrict__ P, T *__restrict__ AUx,
                          T *__restrict__ AUy, T *__restrict__ BUz) {
+    const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 1)
     T *sPv = sF;
     load_tables(G, sD, sDw, sw);
