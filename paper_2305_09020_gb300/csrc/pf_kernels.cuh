@@ -559,6 +559,56 @@ __device__ __forceinline__ void fft_pencils(cplx<T> *buf, int ld, int npen, int 
     }
 }
 
+// The radix-2 DIT of fft_pencils for n = 2^LGZ = 32 or 64, one warp per pencil in registers:
+// lane l holds elements l and l + 32 (bit-reversed order as loaded).  A stage of half span h < 32
+// pairs lanes l and l ^ h (__shfl_xor), the stage of span 64 pairs the two elements of a lane; the
+// butterfly arithmetic is that of fft_pencils.  Called after the block barrier that completes the
+// buffer's loads; ends with a block barrier (the buffer is read by other threads next).
+template <typename T, int LGZ>
+__device__ __forceinline__ void fft_pencils_warp(cplx<T> *buf, int ld, int npen, const cplx<T> *tw, bool inverse) {
+    static_assert(LGZ == 5 || LGZ == 6, "one warp per pencil of 32 or 64 points");
+    constexpr int E = (1 << LGZ) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int pen = warp; pen < npen; pen += nwarp) {
+        cplx<T> *x = buf + pen * ld;
+        cplx<T> v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = x[lane + 32 * e];
+#pragma unroll
+        for (int s = 1; s <= LGZ; ++s) {
+            const int h = 1 << (s - 1);
+            if (h < 32) {
+                cplx<T> w = tw[(lane & (h - 1)) << (LGZ - s)];
+                if (inverse) w.y = -w.y;
+                const bool top = (lane & h) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    cplx<T> pr;
+                    pr.x = __shfl_xor_sync(0xffffffffu, v[e].x, h);
+                    pr.y = __shfl_xor_sync(0xffffffffu, v[e].y, h);
+                    if (top) {
+                        const cplx<T> m = cmul(pr, w);
+                        v[e] = {v[e].x + m.x, v[e].y + m.y};
+                    } else {
+                        const cplx<T> m = cmul(v[e], w);
+                        v[e] = {pr.x - m.x, pr.y - m.y};
+                    }
+                }
+            } else {   // span 64: elements lane and lane + 32 of this lane
+                cplx<T> w = tw[lane];
+                if (inverse) w.y = -w.y;
+                const cplx<T> m = cmul(v[E - 1], w);
+                const cplx<T> u = v[0];
+                v[0] = {u.x + m.x, u.y + m.y};
+                v[E - 1] = {u.x - m.x, u.y - m.y};
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[lane + 32 * e] = v[e];
+    }
+    __syncthreads();
+}
+
 // Stockham autosort FFT of npen pencils of any even length n = 2^a 3^b 5^c 7^d (natural order in
 // and out; the result ends in buf, tmp is scratch of the same shape).  Each stage of radix R
 // (4, 2, 3, 5 or 7, taken in that order while it divides what is left) combines R inputs
@@ -735,7 +785,9 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
         }
     }
     __syncthreads();
-    if (nz > 1) {
+    if constexpr ((LGZ == 5 || LGZ == 6) && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+        fft_pencils_warp<T, LGZ>(buf, ld, tp, stw, false);
+    } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp, nz, stw, false);
         else fft_pencils_mixed(buf, tmp, ld, tp, nz, stw, false);
     }
@@ -859,7 +911,9 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
         }
     }
     __syncthreads();
-    if (nz > 1) {
+    if constexpr ((LGZ == 5 || LGZ == 6) && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+        fft_pencils_warp<T, LGZ>(buf, ld, tp * npair, stw, true);
+    } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp * npair, nz, stw, true);
         else fft_pencils_mixed(buf, tmp, ld, tp * npair, nz, stw, true);
     }
