@@ -566,7 +566,12 @@ struct Engine {
                 // nearly empty 64- or 32-wide one
                 if (simt_tile == 3) {
                     dim3 grid(1, (unsigned)((Mrows + 63) / 64));
+                    // FP32: k tiles of ceil(N / 5) so that five tiles hold N exactly (13 for N = 65)
+                    const int bky = sizeof(T) == 4 ? (Ncol + 4) / 5 : BK;
                     if (vec) pf::k_gemm_cp<T, 64, 80, BK, 4, 4, 4, true><<<grid, 320, 0, st>>>(g);
+                    else if (bky == 13) pf::k_gemm_cp<T, 64, 80, 13, 4, 4, 4, false><<<grid, 320, 0, st>>>(g);
+                    else if (bky == 14) pf::k_gemm_cp<T, 64, 80, 14, 4, 4, 4, false><<<grid, 320, 0, st>>>(g);
+                    else if (bky == 15) pf::k_gemm_cp<T, 64, 80, 15, 4, 4, 4, false><<<grid, 320, 0, st>>>(g);
                     else pf::k_gemm_cp<T, 64, 80, BK, 4, 4, 4, false><<<grid, 320, 0, st>>>(g);
                 } else {
                     dim3 grid(1, (unsigned)((Mrows + 31) / 32));
