@@ -361,7 +361,7 @@ def main():
                          "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,P) + "
                                                  "pf_get_fields(phi,u), pinned host buffers, no host-side copies"}
         if rank == 0 and world == 1:
-            val, secs, desc = oracle_sample(1, 2, args.workload)
+            val, secs, desc = oracle_sample(10, 2, args.workload)   # ~7 s of timed oracle work (droplet3d)
             extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     h.close()
 
