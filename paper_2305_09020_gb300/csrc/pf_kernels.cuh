@@ -1823,7 +1823,14 @@ __global__ void k_cap_solve(Geo<T> G, const T *__restrict__ rhs, const T *__rest
         T acc = 0;
         for (int i = 1; i <= imax; ++i) acc += Ky0[i] * y[base + (long long)i * nx + j];
         T kw = 0;
-        for (int l = 0; l < nx; ++l) kw += Kx[(long long)j * nx + l] * wp[l];
+        if (nx > 2 * G.K) {   // K_x couples j only with the nodes of its element(s): j - K .. j + K
+            for (int d = -G.K; d <= G.K; ++d) {
+                const int l = (j + d + nx) % nx;
+                kw += Kx[(long long)j * nx + l] * wp[l];
+            }
+        } else {
+            for (int l = 0; l < nx; ++l) kw += Kx[(long long)j * nx + l] * wp[l];
+        }
         s[jj] = rhs[base + j] - G.Mx[j] * acc - my0 * kw - G.Mx[j] * c * my0 * wp[j];
     }
     __syncthreads();
@@ -1835,10 +1842,12 @@ __global__ void k_cap_solve(Geo<T> G, const T *__restrict__ rhs, const T *__rest
         d[(long long)p * m + jj] = acc;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < G.n2; q += blockDim.x) {
-        const int i = q / nx, j = q - (q / nx) * nx;
-        const int jj = gapidx[j];
-        rhs2[base + q] = (i >= 1 && jj >= 0) ? Ky0[i] * G.Mx[j] * ds[jj] : T(0);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < ny; i += nw) {
+        for (int j = lane; j < nx; j += 32) {
+            const int jj = gapidx[j];
+            rhs2[base + (long long)i * nx + j] = (i >= 1 && jj >= 0) ? Ky0[i] * G.Mx[j] * ds[jj] : T(0);
+        }
     }
 }
 
