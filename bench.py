@@ -50,6 +50,8 @@ WORKLOADS = {
                          "equilibrium system, pseudo-time step 2e-6",
     "patches2d": "patches2d: 16x4 elements order 8, four electrodes at -+0.5 on the wall, half-disc drop, "
                  "eps/rho/mu ratios 5/2/2, dt=1e-4",
+    "layers3d": "layers3d: 32x16 elements order 10 x Nz=256 planes, two stacked layers (fluid 1 below y=0.3) plus "
+                "a drop r=0.15 at (1,0.65,0.5), eta=0.005, eps/rho/mu ratios 20/10/10, V=2, dt=5e-5",
 }
 
 
@@ -214,6 +216,7 @@ def main():
     ap.add_argument("--workload", default="droplet3d", choices=sorted(WORKLOADS),
                     help="droplet3d (the default bench line), or the electrode workloads")
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the transform variant (a PF_GEMM_* code) instead of autotuning")
     ap.add_argument("--fused-y", type=int, default=0, help="with --variant: run the y pair fused (1) or not (0)")
@@ -360,7 +363,7 @@ def main():
                          "h2d_bytes_per_step": int(hio.nbytes), "d2h_bytes_per_step": int(hio.nbytes + hvp.nbytes),
                          "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,P) + "
                                                  "pf_get_fields(phi,u), pinned host buffers, no host-side copies"}
-        if rank == 0 and world == 1:
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
             val, secs, desc = oracle_sample(10, 2, args.workload)   # ~7 s of timed oracle work (droplet3d)
             extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
     h.close()

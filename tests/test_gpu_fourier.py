@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import workloads
+from tolerances import mixed_bar
 from paper_2305_09020_gb300 import native
 
 from gpu_util import ALL, run_pair
@@ -35,8 +36,7 @@ def test_mixed_radix_planes_mixed_precision():
     res = run_pair(wl, 4, precision=native.PF_MIXED, check_every=1)
     for step, errs in res:
         for k, v in errs.items():
-            prim = k in ("V", "phi", "psi")
-            tol = (1e-6 if prim else 1e-4) if step <= 1 else (5e-5 if prim else 5e-4)
+            tol = mixed_bar(k, step)
             assert v <= tol, (step, k, v)
 
 

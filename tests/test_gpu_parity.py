@@ -1,15 +1,15 @@
 """GPU (CUDA through the C-ABI) versus the FP64 CPU oracle, element by element.
 
-Tolerances (relative L2 per field; absolute max for a field that is identically 0):
+Tolerances (relative L2 per field; absolute max for a field that is identically 0) come from
+tests/tolerances.py, which states why each bar is what it is:
 * FP64 path: <= 1e-11.  The two sides differ only by round-off: fast diagonalisation
   and sparse LU each solve the same assembled systems to ~3e-14 / ~1e-14, and the
   difference grows linearly with the number of steps (about 1e-13 per step on the
   velocity of the 2D droplet, whose update is a small residual of cancelling forces),
   so the 100-step 2D droplet run is held to 1e-11 through step 75 and to 2e-11 at 100.
-* mixed path (FP32 node kernels, FFT and transforms): the primary fields V, phi, psi
-  <= 1e-6 after one step; E, P and u are spectral derivatives of FP32 fields (the
-  GLL derivative amplifies the FP32 unit round-off 6e-8 by ~K^2/h ~ 1e2..1e3), so
-  <= 1e-4 after one step.  After 100 steps: V, phi, psi <= 5e-5, E, P, u <= 5e-4."""
+* mixed path: V, phi, psi <= 1e-6 after one step; E, P, u <= 1e-4 (relaxed; the floors of an
+  FP32 design are measured on the CPU in tests/test_oracle_precision_floor.py).  After 100
+  steps V, phi, psi <= 5e-5 and E, P, u <= 5e-4 (relaxed bars, not the target's 1e-5)."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -19,11 +19,9 @@ from oracle.sem import Mesh2D
 from paper_2305_09020_gb300 import native
 
 from gpu_util import run_pair
+from tolerances import FP64 as FP64_TOL, mixed_bar
 
 pytestmark = pytest.mark.gpu
-
-FP64_TOL = 1e-11
-
 
 def _assert_all(res, tol):
     for step, errs in res:
@@ -91,16 +89,10 @@ def test_step_parity_3d_small_neumann_top():
     _assert_all(run_pair(wl, 4, check_every=2), FP64_TOL)
 
 
-PRIMARY = ("V", "phi", "psi")
-
-
 def _assert_mixed(res, last):
     for step, errs in res:
         for k, v in errs.items():
-            if step <= 1:
-                tol = 1e-6 if k in PRIMARY else 1e-4
-            else:
-                tol = 5e-5 if k in PRIMARY else 5e-4
+            tol = mixed_bar(k, step)
             assert v <= tol, f"step {step}: {k} = {v:.3e} > {tol:.0e}"
     assert res[-1][0] == last
 
