@@ -174,7 +174,9 @@ int pf_create(const pf_mesh *mesh, const pf_fluid *fluid, const pf_vbc *vbc,
 int pf_step(pf_handle *h, int nsteps);
 
 /* Synchronise the handle's stream and check the state for non-finite values:
- * returns PF_EDIVERGED if any was found since creation. */
+ * returns PF_EDIVERGED if any was found since creation.  Returns PF_ETIMEOUT (and clears the
+ * condition) when a bounded device-side wait of the tensor-core transforms gave up since the
+ * last pf_sync; the fields computed by those steps are then not valid. */
 int pf_sync(pf_handle *h);
 
 /* Copy fields to the host (synchronous).  mask: PF_FIELD_* bits; blocks of
@@ -188,10 +190,21 @@ int pf_get_fields(pf_handle *h, unsigned mask, double *host_out, size_t n);
  * next step restarts the BDF history only if reset_history != 0. */
 int pf_set_fields(pf_handle *h, unsigned mask, const double *host_in, size_t n, int reset_history);
 
+/* Restart bookkeeping (Sec. 3.1: the BDF order J of a step is 1 for the first step of a run and
+ * the scheme's order afterwards): set the handle's step count and time.  With both history levels
+ * written by pf_set_fields (mask with and without PF_FIELD_OLD, reset_history = 0) and the step
+ * count and time of the run that wrote them (pf_diagnostics out[3], out[2]), a fresh handle of the
+ * same descriptors continues that run.  PF_EINVAL for nstep < 0 or a non-finite t. */
+int pf_set_step(pf_handle *h, int nstep, double t);
+
 /* FP64 diagnostics (synchronous): out[0] = int phi (phase mass), out[1] = max|u|,
  * out[2] = time t, out[3] = step count, out[4] = number of V^0 fixed-point
  * iterations, out[5] = 1 if a non-finite value was seen, out[6] = max|phi^n - phi^{n-1}| / dt
- * (the pseudo-time rate of the equilibrium model), out[7] = 0. */
+ * (the pseudo-time rate of the equilibrium model), out[7] = the discrete energy E(t) of eq. 14
+ * at the current level: GLL quadrature of rho|u|^2/2 + lambda|grad phi|^2/2 +
+ * lambda (phi^2-1)^2/(4 eta^2) + eps(phi)|E|^2/2 with element-local derivatives (d/dz spectral),
+ * plus the wall energy sigma cos(theta_s) phi (phi^2-3)/4 integrated over the wall (its constant
+ * dropped); FP64 arithmetic and accumulation whatever the precision of the state. */
 int pf_diagnostics(pf_handle *h, double out[8]);
 
 /* One fast-diagonalisation solve on a user right-hand side (synchronous):
@@ -200,7 +213,8 @@ int pf_diagnostics(pf_handle *h, double out[8]);
  * (PF_BCSET_*; for PF_BCSET_V the handle's potential sides).  rhs/out are host
  * arrays of n_x*n_y doubles ([y][x]) for mode 0 (and always in 2D) and two such
  * planes (real, imaginary) for 0 < mode <= Nz/2.  Runs in the handle's precision.
- * Errors: PF_EINVAL for a bad bcset or mode. */
+ * Errors: PF_EINVAL for a bad bcset or mode; PF_ETIMEOUT when a bounded device-side wait of the
+ * tensor-core transforms gave up (the output is then not valid). */
 int pf_solve_helmholtz(pf_handle *h, int bcset, int mode, double lambda,
                        const double *rhs, double *out);
 
@@ -228,7 +242,9 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
 
 /* Transform variants of the fast-diagonalisation solves (Sec. 3.1 solves, Eq. 44/48/52), as
  * codes for pf_set_variant and pf_autotune:
- *   PF_GEMM_TC       3xTF32 tcgen05 tensor-core transforms (PF_MIXED only)
+ *   PF_GEMM_TC       3xTF32 tcgen05 tensor-core transforms: persistent warp-specialised kernel,
+ *                    TMA-staged operands, FP32 sums of per-K-chunk TMEM accumulators (PF_MIXED
+ *                    only; n_x a multiple of 4, for the 16-byte row pitch TMA needs)
  *   PF_GEMM_PLANE    the whole solve of a mode plane in one thread block, plane and eigenbases
  *                    in shared memory (FP32 precisions; n_x <= 128, n_y <= 128)
  *   PF_GEMM_SIMT32 / PF_GEMM_SIMT64 / PF_GEMM_SIMT32X64
@@ -271,6 +287,14 @@ int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);
  * the variant (PF_GEMM_TC outside PF_MIXED, the whole-plane variants in FP64 or on a plane too
  * large). */
 int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile);
+
+/* Test hook of the failure detection (Sec. 3 has no counterpart): the next tensor-core transform
+ * launch of h waits on a device barrier that nothing arrives at, gives up after wait_ns
+ * nanoseconds (0 < wait_ns <= 1e10), records the time-out in the handle's error word and returns
+ * without touching tensor memory; pf_sync (after pf_step) or pf_solve_helmholtz then return
+ * PF_ETIMEOUT.  The next pf_step runs without its captured graph so that the hook applies.
+ * PF_EINVAL when the handle does not use the tensor-core transforms. */
+int pf_debug_tc_stall(pf_handle *h, unsigned long long wait_ns);
 
 /* Geometry queries: nodes_x[n_x], nodes_y[n_y] (either may be NULL), sizes in dims[4]
  * = {n_x, n_y, Nz, number of real values per field}. */

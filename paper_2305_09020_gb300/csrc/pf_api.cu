@@ -10,7 +10,9 @@
 //   k_momentum -> k_fwd -> FDM (P) -> k_inv (P)
 //   k_ugradp -> k_fwd (all components) -> FDM (u, batched) -> k_inv (all components)
 // The new level is written over level n-1, then the two levels swap roles.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdio>
@@ -52,6 +54,30 @@ void raise_smem_limit(const void *fn, size_t bytes) {
     PF_CU(cudaFuncGetAttributes(&fa, fn));
     if ((size_t)fa.maxDynamicSharedSizeBytes < bytes)
         PF_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link against libcuda); null when
+// the driver does not provide it
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiled tc_encode() {
+    static EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    PF_CU(cudaGetDevice(&dev));
+    PF_CU(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    return n;
 }
 
 struct HostSetup {
@@ -189,16 +215,31 @@ struct Engine {
     double *red;
     int *dev_err;   // device error word (bounded waits)
     int cur = 0;
-    // 3xTF32 tensor-core operands: for each B matrix of the transforms, B^T split into
-    // TF32 head/tail, zero padded to Npad x Kpad
+    // 3xTF32 tensor-core transforms: for each B matrix (an eigenbasis or its transpose), B^T split
+    // into TF32 head and tail, zero padded to Npad x Kpad, with its TMA descriptors
     struct TcB {
         const T *key;
         float *hi, *lo;
-        int N, Npad, Kpad, ntile, tile_n, cols;
+        int N, BN, BNlast, ntn, Npad, Kpad, stages, tmem_cols;
         size_t smem;
+        CUtensorMap mh, ml;
     };
     std::vector<TcB> tcb;
     bool use_tc = false;
+    int tc_group = 1;                 // K chunks (of 32) per TMEM accumulation group
+    int tc_stall = 0;                 // test hook: the next tensor-core launch reports a time-out
+    unsigned long long tc_wait_ns = 1000000000ull;   // bound of every wait (1 s)
+    unsigned long long tc_wait_ns_next = 0;          // the test hook's bound
+    int nyp = 0;                      // row pitch of the y-transform intermediates (multiple of 4)
+    int sms = 0;                      // multiprocessors of the device (persistent grid)
+    // TMA descriptors of the A operands, by (base, rows, K, pitch)
+    struct AMap {
+        const void *ptr;
+        long long rows;
+        int K, pitch;
+        CUtensorMap map;
+    };
+    std::vector<AMap> amaps;
     int simt_tile = 0;   // SIMT GEMM tile: 0 heuristic, 32 or 64 forced (autotuner)
     int tp_override = 0; // pencils per transform block: 0 heuristic, else forced (autotuner)
     // steady-state (BDF2) step captured once per history-slot parity; replayed by pf_step
@@ -364,7 +405,9 @@ struct Engine {
             }
         }
         faceU = mk<T>((size_t)ex * p * nz);
-        RHS = mk<T>(3 * N); OUT = mk<T>(3 * N); W1 = mk<T>(3 * N); W2 = mk<T>(3 * N);
+        nyp = (ny + 3) / 4 * 4;
+        RHS = mk<T>(3 * N); OUT = mk<T>(3 * N);
+        W1 = mk<T>((size_t)3 * nz * nx * nyp); W2 = mk<T>((size_t)3 * nz * nx * nyp);
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
         if (fdm_y_smem() > 48 * 1024 && fdm_y_smem() <= 200 * 1024)
             raise_smem_limit((const void *)pf::k_fdm_y<T, 32, 8>, fdm_y_smem());
@@ -390,7 +433,7 @@ struct Engine {
 
         red = mk<double>(std::max<long long>(1024, nz));
         dev_err = mk<int>(1);
-        use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED;
+        use_tc = (sizeof(T) == 4) && s.precision == PF_MIXED && tc_possible();
         if (use_tc) {
             // B = Sx (Bt = Sx^T), B = Sx^T (Bt = Sx), B = Sy (Bt = Sy^T), B = Sy^T (Bt = Sy)
             auto tr = [](const std::vector<double> &m, int n) {
@@ -405,7 +448,9 @@ struct Engine {
                 add_tc(Sy[b], tr(s.Sy[b], ny), ny);
                 add_tc(SyT[b], s.Sy[b], ny);
             }
-            raise_smem_limit((const void *)pf::k_gemm_tc<16>, tc_smem(16));
+            size_t most = 0;
+            for (auto &t : tcb) most = std::max(most, t.smem);
+            raise_smem_limit((const void *)pf::k_gemm_tc, most);
         }
         PF_CU(cudaStreamSynchronize(st));
     }
@@ -420,15 +465,46 @@ struct Engine {
         return r;
     }
 
-    // Bt (n x n row-major, FP64) -> TF32 head/tail on the device, rows padded to a multiple of 64
-    // (the column tiles) and K padded to a multiple of 32 (the chunks)
+    // the tensor-core transforms need 16-byte row pitches for TMA: n_x a multiple of 4 (the
+    // right-hand sides and solutions keep pitch n_x; the y intermediates are padded to nyp)
+    bool tc_possible() const { return nx % 4 == 0 && tc_encode() != nullptr; }
+
+    // column tiles of an N-column product: full tiles of BN = min(2 TC_MAXH, N rounded up to 16)
+    // columns and a last one that holds the rest (a multiple of 16)
+    static int tc_bn(int n, int *ntn, int *bnlast) {
+        const int npad = (n + 15) / 16 * 16;
+        const int bn = std::min(2 * pf::TC_MAXH, npad);
+        *ntn = (npad + bn - 1) / bn;
+        *bnlast = npad - (*ntn - 1) * bn;
+        return bn;
+    }
+
+    static void encode_2d(CUtensorMap *m, const void *ptr, long long rows, int K, int pitch, int box_rows) {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+        cuuint32_t box[2] = {(cuuint32_t)pf::TC_KC, (cuuint32_t)box_rows};
+        cuuint32_t estr[2] = {1, 1};
+        const CUresult r = tc_encode()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides,
+                                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
+    }
+
+    // Bt (n x n row-major, FP64) -> TF32 head/tail on the device, padded to ntn BN rows and to
+    // whole K chunks of 32, with the TMA descriptors of both halves
     void add_tc(const T *key, const std::vector<double> &Bt, int n) {
         TcB t;
         t.key = key;
         t.N = n;
-        t.Npad = (n + 63) / 64 * 64;
-        t.Kpad = (n + 31) / 32 * 32;
-        t.ntile = 0; t.tile_n = 0; t.cols = 0; t.smem = 0;
+        t.BN = tc_bn(n, &t.ntn, &t.BNlast);
+        t.Npad = (t.ntn - 1) * t.BN + t.BNlast;
+        t.Kpad = (n + pf::TC_KC - 1) / pf::TC_KC * pf::TC_KC;
+        const size_t stage = (size_t)2 * pf::TC_BM * pf::TC_KC * 4 + (size_t)2 * t.BN * pf::TC_KC * 4;
+        const size_t fixed = 1024 + 256;   // alignment slack, barriers, TMEM slot, abort flag
+        t.stages = (int)std::min<size_t>(4, (size_t)(227 * 1024 - fixed) / stage);
+        t.smem = t.stages * stage + fixed;
+        t.tmem_cols = 32;
+        while (t.tmem_cols < 2 * t.BN) t.tmem_cols *= 2;
         std::vector<float> hi((size_t)t.Npad * t.Kpad, 0.f), lo((size_t)t.Npad * t.Kpad, 0.f);
         for (int r = 0; r < n; ++r)
             for (int k = 0; k < n; ++k) {
@@ -442,15 +518,69 @@ struct Engine {
         PF_CU(cudaMemcpyAsync(t.hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, st));
         PF_CU(cudaMemcpyAsync(t.lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
         PF_CU(cudaStreamSynchronize(st));
+        encode_2d(&t.mh, t.hi, t.Npad, t.Kpad, t.Kpad, t.BN);
+        encode_2d(&t.ml, t.lo, t.Npad, t.Kpad, t.Kpad, t.BN);
         tcb.push_back(t);
     }
 
-    // dynamic shared memory of k_gemm_tc<TN>: two stages of A and Bt (hi, lo), barrier, slack;
-    // at least a third of the SM so that at most two CTAs (2 x 16 TN <= 512 TMEM columns for
-    // TN <= 16) share one
-    static size_t tc_smem(int TN) {
-        const size_t need = (size_t)2 * (2 * 128 * 32 * 4 + 2 * TN * 32 * 4) + 16 + 1024;
-        return std::max(need, (size_t)233472 / 3 + 1024);
+    const CUtensorMap &amap(const T *ptr, long long rows, int K, int pitch) {
+        for (auto &a : amaps)
+            if (a.ptr == ptr && a.rows == rows && a.K == K && a.pitch == pitch) return a.map;
+        AMap a;
+        a.ptr = ptr; a.rows = rows; a.K = K; a.pitch = pitch;
+        encode_2d(&a.map, ptr, rows, K, pitch, pf::TC_BM);
+        amaps.push_back(a);
+        return amaps.back().map;
+    }
+
+    // C = A B on the tensor cores (B one of the eigenbases registered by add_tc); A has `rows` rows
+    // of K values at pitch lda; epilogue as pf::TcArgs
+    void gemm_tc(const T *A, int lda, const T *B, T *C, long long rows, int R, int store, int ldc, int ldr,
+                 const T *lamN, const T *lamR, const T *cpl, int cpl_mod, T *C2 = nullptr, const T *face2 = nullptr) {
+        const TcB *tb = nullptr;
+        for (auto &t : tcb)
+            if (t.key == B) tb = &t;
+        if (!tb) throw CudaError{cudaErrorInvalidValue, "tensor-core transform without its eigenbasis"};
+        pf::TcArgs a{};
+        if (rows >= (1ll << 31)) throw CudaError{cudaErrorInvalidValue, "tensor-core transform with 2^31 rows"};
+        a.M = (int)rows; a.N = tb->N; a.BN = tb->BN; a.BNlast = tb->BNlast; a.ntn = tb->ntn;
+        a.nchunk = tb->Kpad / pf::TC_KC;
+        a.group = tc_group; a.stages = tb->stages; a.tmem_cols = tb->tmem_cols;
+        a.ntiles = (int)((rows + pf::TC_BM - 1) / pf::TC_BM * tb->ntn);
+        a.R = R; a.store = store; a.ldc = ldc; a.ldr = ldr;
+        a.lamN = reinterpret_cast<const float *>(lamN);
+        a.lamR = reinterpret_cast<const float *>(lamR);
+        a.cpl = reinterpret_cast<const float *>(cpl);
+        a.cpl_mod = cpl_mod;
+        a.C = reinterpret_cast<float *>(C);
+        a.C2 = reinterpret_cast<float *>(C2);
+        a.m2x = reinterpret_cast<const float *>(Mx);
+        a.m2y = reinterpret_cast<const float *>(My);
+        a.face2 = reinterpret_cast<const float *>(face2);
+        a.err = dev_err;
+        a.wait_ns = tc_stall ? tc_wait_ns_next : tc_wait_ns;
+        a.stall = tc_stall;
+        tc_stall = 0;
+        const CUtensorMap &ma = amap(A, rows, tb->N, lda);
+        if (sms == 0) sms = num_sms();
+        const unsigned grid = (unsigned)std::min(a.ntiles, sms);
+        prof->begin(PF_KC_GEMM, st);
+        pf::k_gemm_tc<<<grid, pf::TC_THREADS, tb->smem, st>>>(ma, tb->mh, tb->ml, a);
+        check_launch();
+        prof->end(st);
+    }
+
+    // fast-diagonalisation solve on the tensor cores: the four transforms of fdm() with the y
+    // intermediates at row pitch nyp (16-byte rows for TMA)
+    void fdm_tc(const T *rhs, T *out, int bcset, const T *sh, long long P, T *minus_m_out, const T *face) {
+        // x: W1[p][x][y] (pitch nyp) = (rhs[p][y][:] Sx)^T
+        gemm_tc(rhs, nx, Sx, W1, P * ny, ny, 1, 0, nyp, nullptr, nullptr, nullptr, 1);
+        // y with the eigenvalue division: W2[p][x][:] = (W1[p][x][:] Sy) / (Ly + Lx + shift)
+        gemm_tc(W1, nyp, Sy[bcset], W2, P * nx, nx, 0, nyp, 0, Ly[bcset], Lx, sh, nz);
+        // y^T: W1[p][y][x] (pitch nx) = (W2[p][x][:] Sy^T)^T
+        gemm_tc(W2, nyp, SyT[bcset], W1, P * nx, nx, 1, 0, nx, nullptr, nullptr, nullptr, 1);
+        // x^T: out[p][y][:] = W1[p][y][:] Sx^T (and the phi right-hand side -M psi (+ wall term))
+        gemm_tc(W1, nx, SxT, out, P * ny, ny, 0, nx, 0, nullptr, nullptr, nullptr, 1, minus_m_out, face);
     }
 
     ~Engine() {
@@ -529,32 +659,6 @@ struct Engine {
 
     void gemm(const T *A, const T *B, T *C, long long Mrows, int Ncol, int R, int store, const T *lamN,
               const T *lamR, const T *cpl, int cpl_mod, T *C2 = nullptr, const T *face2 = nullptr) {
-        if (use_tc) {
-            for (auto &t : tcb) {
-                if (t.key != B) continue;
-                pf::TcArgs a;
-                a.A = reinterpret_cast<const float *>(A);
-                a.Bhi = t.hi; a.Blo = t.lo;
-                a.C = reinterpret_cast<float *>(C);
-                a.Mrows = Mrows; a.Kd = Ncol; a.N = Ncol; a.Npad = t.Npad; a.Kpad = t.Kpad;
-                a.ntile = 0; a.tile_n = 0; a.tmem_cols = 0;
-                a.R = R; a.store = store;
-                a.lamN = reinterpret_cast<const float *>(lamN);
-                a.lamR = reinterpret_cast<const float *>(lamR);
-                a.cpl = reinterpret_cast<const float *>(cpl);
-                a.cpl_mod = cpl_mod; a.err = dev_err;
-                a.C2 = reinterpret_cast<float *>(C2);
-                a.m2x = reinterpret_cast<const float *>(Mx);
-                a.m2y = reinterpret_cast<const float *>(My);
-                a.face2 = reinterpret_cast<const float *>(face2);
-                const unsigned mt = (unsigned)((Mrows + 127) / 128);
-                prof->begin(PF_KC_GEMM, st);
-                pf::k_gemm_tc<16><<<dim3(mt, (Ncol + 15) / 16), 128, tc_smem(16), st>>>(a);
-                check_launch();
-                prof->end(st);
-                return;
-            }
-        }
         pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod, C2, Mx, My, face2};
         constexpr int BK = sizeof(T) == 8 ? 8 : 16;
         if (simt_tile >= 3 && simt_tile <= 5) {   // cp.async pipelines: 64x64, 32x32, 32x64 tiles
@@ -686,6 +790,10 @@ struct Engine {
     void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
              const T *face = nullptr) {
         const long long P = nplanes;
+        if (use_tc && !tcb.empty()) {
+            fdm_tc(rhs, out, bcset, sh, P, minus_m_out, face);
+            return;
+        }
         if (cluster && cluster_fits(cluster)) {
             prof->begin(PF_KC_GEMM, st);
             if (cluster == 4) cluster_cq<4>(rhs, out, bcset, sh, P, minus_m_out, face);
@@ -945,6 +1053,36 @@ struct Engine {
         check_launch();
         PF_CU(cudaMemcpyAsync(out, red, nz * sizeof(double), cudaMemcpyDeviceToHost, st));
         PF_CU(cudaStreamSynchronize(st));
+    }
+
+    // discrete energy E(t) of eq. 14 at level n (FP64; synchronous)
+    double *epart = nullptr;
+    double energy() {
+        const dim3 grid = elem_grid();
+        const size_t nb = (size_t)grid.x * grid.y;
+        if (!epart) epart = mk<double>(nb);
+        pf::EnergyConst c{hs.rho1, hs.rho2, hs.eps1, hs.eps2, hs.lam, 1.0 / (hs.eta * hs.eta),
+                          hs.sigma * hs.cos_theta};
+        const int n = cur;
+        pf::k_energy<T><<<grid, elem_threads(), elem_smem(1), st>>>(geo(), c, phi[n], d3 ? dzphi[n] : nullptr, u[0][n],
+                                                                   u[1][n], d3 ? u[2][n] : nullptr, Ex, Ey,
+                                                                   d3 ? Ez[n] : nullptr, epart);
+        check_launch();
+        std::vector<double> h(nb);
+        PF_CU(cudaMemcpyAsync(h.data(), epart, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PF_CU(cudaStreamSynchronize(st));
+        double acc = 0.0;
+        for (double v : h) acc += v;
+        return acc * (d3 ? hs.lz / nz : 1.0);
+    }
+
+    // error word of the bounded device waits: read (synchronous) and clear
+    int take_err() {
+        int e = 0;
+        PF_CU(cudaMemcpyAsync(&e, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PF_CU(cudaStreamSynchronize(st));
+        if (e) PF_CU(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+        return e;
     }
 
     // ---- reductions (FP64 accumulation) -------------------------------------------------------
@@ -1248,7 +1386,7 @@ int do_steps(pf_handle *h, Engine<T> &E, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         const int J = (h->nstep == 0 || h->hs.bdf == 1) ? 1 : 2;
         // graphs need a capturable stream (not the legacy default stream) and no event timers
-        if (J == 2 && E.st != nullptr && !h->prof.on) E.step_graph();
+        if (J == 2 && E.st != nullptr && !h->prof.on && !E.tc_stall) E.step_graph();
         else E.step(J);
         h->last_J = J;
         h->nstep += 1;
@@ -1413,6 +1551,9 @@ int sync_impl(pf_handle *h, Engine<T> &E) {
     double um = 0.0;
     for (int c = 0; c < 3; ++c)
         if (E.u[c][n]) um = std::max(um, E.reduce(E.u[c][n], nullptr, 1));
+    if (E.take_err())
+        return fail(h, PF_ETIMEOUT, "a tensor-core transform gave up waiting (bounded mbarrier wait); the state "
+                                    "of the steps since the last pf_sync is not valid");
     if (!(m == m) || !(um == um) || std::isinf(m) || std::isinf(um)) h->diverged = true;
     return h->diverged ? fail(h, PF_EDIVERGED, "non-finite value in the state") : PF_OK;
 }
@@ -1542,7 +1683,7 @@ int diag_impl(pf_handle *h, Engine<T> &E, double *out) {
     if (!(out[0] == out[0]) || !(um == um)) h->diverged = true;
     out[5] = h->diverged ? 1.0 : 0.0;
     out[6] = E.reduce(E.phi[n], E.phi[1 - n], 2) / h->hs.dt;
-    out[7] = 0.0;
+    out[7] = E.energy();
     return PF_OK;
 }
 
@@ -1566,6 +1707,7 @@ int helm_impl(pf_handle *h, Engine<T> &E, int bcset, int mode, double lambda, co
     PF_CU(cudaMemcpyAsync(o.data(), E.OUT, o.size() * sizeof(T), cudaMemcpyDeviceToHost, E.st));
     PF_CU(cudaStreamSynchronize(E.st));
     for (size_t i = 0; i < o.size(); ++i) out[i] = (double)o[i];
+    if (E.take_err()) return fail(h, PF_ETIMEOUT, "a tensor-core transform gave up waiting (bounded mbarrier wait)");
     return PF_OK;
 }
 }  // namespace
@@ -1735,6 +1877,24 @@ extern "C" int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile) {
     } catch (const CudaError &e) {
         return cuda_fail(h, e);
     }
+    return PF_OK;
+}
+
+extern "C" int pf_set_step(pf_handle *h, int nstep, double t) {
+    if (!h) return PF_EINVAL;
+    if (nstep < 0 || !std::isfinite(t)) return fail(h, PF_EINVAL, "nstep must be >= 0 and t finite");
+    h->nstep = nstep;
+    h->t = t;
+    return PF_OK;
+}
+
+extern "C" int pf_debug_tc_stall(pf_handle *h, unsigned long long wait_ns) {
+    if (!h) return PF_EINVAL;
+    if (!h->e32 || !h->e32->use_tc || h->e32->tcb.empty())
+        return fail(h, PF_EINVAL, "the handle does not run its transforms on the tensor cores");
+    if (wait_ns == 0 || wait_ns > 10000000000ull) return fail(h, PF_EINVAL, "wait_ns must be in (0, 1e10]");
+    h->e32->tc_stall = 1;
+    h->e32->tc_wait_ns_next = wait_ns;
     return PF_OK;
 }
 

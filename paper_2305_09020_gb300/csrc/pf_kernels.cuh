@@ -1910,6 +1910,62 @@ __global__ void k_reduce(const T *__restrict__ x, const T *__restrict__ y, const
     if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
 
+// ---- eq. 14: the discrete energy E(t) (diagnostic; FP64 arithmetic and accumulation) -------
+// Per element, with GLL quadrature and element-local derivatives:
+//   sum_{a,b} w_a w_b (h_x/2)(h_y/2) [ rho(phi)|u|^2/2 + lambda|grad phi|^2/2
+//                                       + lambda (phi^2 - 1)^2 / (4 eta^2) + eps(phi)|E|^2/2 ]
+// plus, on the wall row of the wall elements, sum_a w_a (h_x/2) Theta(phi) with
+// Theta = sigma cos(theta_s) phi (phi^2 - 3)/4 (eq. theta_def, constant dropped).  3D: d/dz phi is
+// the spectral derivative at the node; the caller multiplies by the plane weight Lz/Nz.
+// One partial sum per block (blockIdx.y = plane), summed in order on the host.
+struct EnergyConst {
+    double rho1, rho2, eps1, eps2, lam, inv_eta2, sigma_cos;
+};
+
+template <typename T>
+__global__ void k_energy(Geo<T> G, EnergyConst c, const T *__restrict__ phi, const T *__restrict__ dzphi,
+                         const T *__restrict__ ux, const T *__restrict__ uy, const T *__restrict__ uz,
+                         const T *__restrict__ Ex, const T *__restrict__ Ey, const T *__restrict__ Ez,
+                         double *__restrict__ part) {
+    PF_ELEM_SMEM(T, G, 1)
+    T *sP = sF;
+    load_tables(G, sD, sDw, sw);
+    const ElemIdx e = elem_index(G);
+    if (e.act) sP[e.t] = phi[e.g];
+    __syncthreads();
+    double v = 0.0;
+    if (e.act) {
+        const double hx = (double)G.hx[e.ex], hy = (double)G.hy[e.ey];
+        double gx = 0.0, gy = 0.0;
+        for (int m = 0; m < G.p; ++m) {
+            gx += (double)sD[e.a * G.p + m] * (double)sP[e.b * G.p + m];
+            gy += (double)sD[e.b * G.p + m] * (double)sP[m * G.p + e.a];
+        }
+        gx *= 2.0 / hx;
+        gy *= 2.0 / hy;
+        const double gz = dzphi ? (double)dzphi[e.g] : 0.0;
+        const double f = (double)phi[e.g];
+        const double u0 = (double)ux[e.g], u1 = (double)uy[e.g], u2 = uz ? (double)uz[e.g] : 0.0;
+        const double e0 = (double)Ex[e.g], e1 = (double)Ey[e.g], e2 = Ez ? (double)Ez[e.g] : 0.0;
+        const double rho = 0.5 * (c.rho1 + c.rho2) + 0.5 * (c.rho1 - c.rho2) * f;
+        const double eps = 0.5 * (c.eps1 + c.eps2) + 0.5 * (c.eps1 - c.eps2) * f * (3.0 - f * f) / 2.0;
+        const double w2 = f * f - 1.0;
+        const double dens = 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2) + 0.5 * c.lam * (gx * gx + gy * gy + gz * gz) +
+                            c.lam * c.inv_eta2 / 4.0 * w2 * w2 + 0.5 * eps * (e0 * e0 + e1 * e1 + e2 * e2);
+        v = (double)sw[e.a] * (double)sw[e.b] * (0.5 * hx) * (0.5 * hy) * dens;
+        if (e.ey == 0 && e.b == 0) v += (double)sw[e.a] * (0.5 * hx) * c.sigma_cos * f * (f * f - 3.0) / 4.0;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
 template <typename T, typename S>
 __global__ void k_convert(const T *__restrict__ in, S *__restrict__ out, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -1,62 +1,79 @@
-// Tensor-core (tcgen05, sm_103a) GEMM for the single-precision fast-diagonalisation transforms.
+// Tensor-core (tcgen05, sm_103a) GEMM for the single-precision fast-diagonalisation transforms
+// (the constant eigenbasis products of the Remark after Algorithm 2).
 //
-// C[M x N] = A[M x Kd] * B[Kd x N] in "3xTF32": every operand is split into a TF32 head and a
-// TF32 tail (x = hi + lo, both rounded to nearest), and the three products hi*hi, hi*lo, lo*hi
-// accumulate in FP32 in tensor memory; the dropped lo*lo term is ~2^-22 relative, so the result
-// has single-precision accuracy.  B (an eigenbasis, constant for the run) is split once on the
-// host and stored transposed and zero-padded as Bt[Npad][Kpad]; A is split while it is staged.
+// C[M x N] = A[M x K] * B[K x N] in "3xTF32": A and B are split into TF32 heads and tails
+// (x = hi + lo, both rounded to nearest) and the tensor core accumulates hi*hi + hi*lo + lo*hi in
+// FP32; the dropped lo*lo term is ~2^-22 relative, so the product has single-precision accuracy.
+// B (an eigenbasis, constant for the run) is split once on the host and stored transposed and
+// zero padded as Bt[Npad][Kpad] (K-major); A is split in shared memory after it lands.
 //
-// One CTA (4 warps) owns 128 rows of A and a tile of TN columns: per 32-wide K chunk the threads
-// stage A (hi, lo) and Bt (hi, lo) into shared memory in the K-major 128-byte-swizzled layout,
-// one thread issues the MMAs (M = 128, N = TN, K = 8 per instruction) and commits them to an
-// mbarrier.  For every 8-wide K slice the hi*hi product goes to its own TMEM region and the two
-// small correction products to another, so the tensor core never adds a large term to a
-// running sum; the regions are read back with tcgen05.ld and summed in FP32 registers with
-// round-to-nearest.  The epilogue divides by the eigenvalue sum and/or stores per plane.
-// Every wait on the mbarrier is bounded; on time-out the kernel records an error code and
-// returns after freeing its tensor memory.
+// Persistent, warp-specialised kernel; one CTA per SM walks tiles of 128 rows x BN columns:
+//   warp 8      TMA producer: per 32-wide K chunk, A (128 x 32) and both halves of Bt (BN x 32)
+//               into a ring of shared-memory stages (128-byte swizzle, the layout the MMA reads)
+//   warps 0-7   split each landed A chunk into hi (in place) and lo (a second buffer); drain the
+//               TMEM accumulators into FP32 registers and run the epilogue
+//   warp 9      one thread issues tcgen05.mma (M = 128, N = BN, K = 8) and commits to mbarriers
+// The tensor core's FP32 accumulation is not rounded to nearest, and the eigenvector sums cancel
+// heavily, so a long chain of MMAs in one accumulator loses digits.  Each group of `group` K chunks
+// therefore accumulates into its own TMEM region (two regions, ping-pong: the MMAs of group g+1
+// run while warps 0-7 add group g into registers with round-to-nearest), and within a group the
+// small correction products go first.  Every mbarrier wait is bounded (globaltimer); on time-out
+// the kernel records an error word, lets its own copies and MMAs finish (bounded), frees its
+// tensor memory and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace pf {
 
+constexpr int TC_BM = 128;                          // rows per tile = TMEM lanes
+constexpr int TC_KC = 32;                           // K per stage: one 128-byte row of FP32
+constexpr int TC_EPI_WARPS = 8;                     // two warpgroups, one per column half
+constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
+constexpr int TC_MAXH = 64;                         // accumulator columns per thread: BN <= 128
+constexpr int TC_ERR_TIMEOUT = 1;                   // error word: a bounded wait gave up
+
 struct TcArgs {
-    const float *A;           // M x Kd row-major
-    const float *Bhi, *Blo;   // Npad x Kpad row-major (B transposed, split, zero padded)
-    float *C;
-    long long Mrows;
-    int Kd, N, Npad, Kpad;
-    int ntile, tile_n;        // unused by the column-tiled kernel (kept for the launch helper)
-    int tmem_cols;
-    int R, store;             // epilogue as in GemmArgs
-    const float *lamN, *lamR, *cpl;
+    int M;                    // rows of A and C (< 2^31)
+    int N;                    // columns of C
+    int BN;                   // column tile, multiple of 16, <= 2 TC_MAXH (128)
+    int BNlast;               // width of the last column tile (multiple of 16, <= BN)
+    int ntn;                  // column tiles
+    int nchunk;               // K chunks of 32 (Kpad / 32)
+    int group;                // K chunks per TMEM accumulation group
+    int stages;               // shared-memory stages
+    int tmem_cols;            // allocated TMEM columns (power of two >= 2 BN)
+    int ntiles;               // row tiles x column tiles
+    // epilogue: row m = p R + r; store 0: C[m ldc + n]; store 1: C[(p N + n) ldr + r]
+    int R, store, ldc, ldr;
+    const float *lamN, *lamR, *cpl;   // optional division by lamN[n] + lamR[r] + cpl[p % cpl_mod]
     int cpl_mod;
-    int *err;                 // set to 1 when a bounded wait gives up
-    float *C2;                // optional: C2 = -m2x[n] m2y[r] C (+ face2[p N + n] on row r == 0)
+    float *C;
+    float *C2;                // optional C2[m ldc + n] = -m2x[n] m2y[r] C (+ face2[p N + n] on r == 0)
     const float *m2x, *m2y, *face2;
+    int *err;                 // error word (TC_ERR_TIMEOUT)
+    unsigned long long wait_ns;   // bound of every wait
+    int stall;                // test hook: wait on a barrier that nothing arrives at, then report
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// round to nearest TF32 (10 explicit mantissa bits), kept in an FP32 container
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
 
-// K-major, 128-byte swizzle, 8-row atoms of 1024 bytes: descriptor of a tile starting at addr
+// K-major, 128-byte swizzle, 8-row atoms of 1024 bytes: matrix descriptor of a tile at addr
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
-    d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused: swizzled K-major)
     d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
-    d |= (uint64_t)2 << 61;                         // swizzle: 128 bytes
+    d |= (uint64_t)2 << 61;                         // 128-byte swizzle
     return d;
 }
 
@@ -79,185 +96,327 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` to complete.  Gives up (false) after limit_ns of waiting, or at
+// once when another thread of the CTA has raised the abort flag (abort may be null).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort,
+                                          unsigned long long limit_ns) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((it & 31u) == 31u) {
+            if (abort && *abort) return false;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
     }
-    return false;
 }
 
-// byte offset of element (row r, k) in a 32-wide K chunk stored K-major with 128B swizzle
-__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// One CTA: 128 rows of A x TN columns (blockIdx.y selects the column tile).  K is walked in
-// 32-wide chunks, double-buffered: while the tensor core multiplies chunk c the threads stage
-// chunk c+1.  Each chunk writes into one of two TMEM buffers (8 regions each) and is added to
-// FP32 registers (round to nearest) after it completes.
-template <int TN>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(TcArgs g) {
-    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int ABYTES = 128 * 32 * 4;          // one A chunk (hi or lo)
-    constexpr int BBYTES = TN * 32 * 4;           // one Bt chunk (hi or lo)
-    constexpr int STAGE = 2 * ABYTES + 2 * BBYTES;
-    uint64_t *mbar = (uint64_t *)(base + 2 * STAGE);
-    uint32_t *tslot = (uint32_t *)(mbar + 1);
+// 2D tiled TMA load of the box at (x = inner coordinate, y = row) into shared memory
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+              const __grid_constant__ CUtensorMap tmBl, TcArgs g) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    const int S = g.stages, BN = g.BN;
+    const uint32_t ABYTES = TC_BM * TC_KC * 4, BBYTES = (uint32_t)BN * TC_KC * 4;
+    const uint32_t STAGE = 2 * ABYTES + 2 * BBYTES;
+    uint64_t *bars = (uint64_t *)(base + (size_t)S * STAGE);
+    // barriers: full[S] (TMA landed), conv[S] (A split), empty[S] (MMAs done with the stage),
+    // rfull[2] (a group's MMAs done), rempty[2] (a group drained), stall
+    const uint32_t b_full = smem_u32(bars), b_conv = b_full + 8 * S, b_empty = b_conv + 8 * S;
+    const uint32_t b_rfull = b_empty + 8 * S, b_rempty = b_rfull + 16, b_stall = b_rempty + 16;
+    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 5);
+    volatile int *abort_flag = (volatile int *)(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long m0 = (long long)blockIdx.x * 128;
-    const int n0 = blockIdx.y * TN;
-    // TMEM: 2 buffers x 4 K-slices x {hi*hi, lo*hi + hi*lo} regions of TN columns
-    constexpr uint32_t NREG = 8;
-    constexpr uint32_t TCOLS = (2 * NREG * TN < 32) ? 32 : 2 * NREG * TN;
 
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(b_full + 8 * s, 1);
+            mbar_init(b_conv + 8 * s, TC_EPI_WARPS);
+            mbar_init(b_empty + 8 * s, 1);
+        }
+        for (int r = 0; r < 2; ++r) {
+            mbar_init(b_rfull + 8 * r, 1);
+            mbar_init(b_rempty + 8 * r, TC_EPI_WARPS);
+        }
+        mbar_init(b_stall, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (g.stall) {   // test hook: nothing arrives at b_stall; report the time-out and leave
+        __syncthreads();
+        if (tid == 0 && !mbar_wait(b_stall, 0u, abort_flag, g.wait_ns)) atomicExch(g.err, TC_ERR_TIMEOUT);
+        return;
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TCOLS)
+                     "r"(g.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = idesc_tf32(128, TN);
-    const int nchunk = g.Kpad / 32;
-
-    // stage chunk c: every load of the chunk is issued before the first dependent store
-    auto stage = [&](int c) {
-        unsigned char *sb = base + (c & 1) * STAGE;
-        const int k0 = c * 32;
-        const int kk = k0 + lane;            // warp w loads rows w, w+4, ..., column k0 + lane
-        const bool kin = kk < g.Kd;
-        float av[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const long long m = m0 + warp + 4 * i;
-            av[i] = (kin && m < g.Mrows) ? __ldg(g.A + m * g.Kd + kk) : 0.f;
-        }
-        constexpr int NB = TN * 8 / 128;     // float4 chunks of Bt per thread (hi and lo each)
-        float4 bh[NB], bl[NB];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const int idx = tid + 128 * i, r = idx >> 3, q = idx & 7;
-            const long long row = n0 + r;    // < Npad: the column tiles cover Npad exactly
-            bh[i] = __ldg((const float4 *)(g.Bhi + row * g.Kpad + k0 + q * 4));
-            bl[i] = __ldg((const float4 *)(g.Blo + row * g.Kpad + k0 + q * 4));
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const float hi = tf32_rna(av[i]);
-            const float lo = tf32_rna(av[i] - hi);
-            const uint32_t off = sw128_off(warp + 4 * i, lane);
-            *(float *)(sb + off) = hi;
-            *(float *)(sb + ABYTES + off) = lo;
-        }
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const int idx = tid + 128 * i, r = idx >> 3, q = idx & 7;
-            const uint32_t off = sw128_off(r, q * 4);
-            *(float4 *)(sb + 2 * ABYTES + off) = bh[i];
-            *(float4 *)(sb + 2 * ABYTES + BBYTES + off) = bl[i];
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    };
-    auto issue = [&](int c) {   // thread 0 only
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sb = smem_u32(base + (c & 1) * STAGE);
-        const uint32_t aH = sb, aL = sb + ABYTES, bH = sb + 2 * ABYTES, bL = sb + 2 * ABYTES + BBYTES;
-        const uint32_t d = tmem + (uint32_t)((c & 1) * NREG * TN);
-        for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t o = (uint32_t)(kk * 32);
-            const uint32_t dm = d + (uint32_t)(2 * kk * TN), dc = dm + (uint32_t)TN;
-            mma_tf32(dc, sdesc_sw128(aL + o), sdesc_sw128(bH + o), idesc, 0u);   // corrections
-            mma_tf32(dc, sdesc_sw128(aH + o), sdesc_sw128(bL + o), idesc, 1u);
-            mma_tf32(dm, sdesc_sw128(aH + o), sdesc_sw128(bH + o), idesc, 0u);   // main term alone
-        }
-        mma_commit(smem_u32(mbar));
+    const int nchunk = g.nchunk;
+    const int my_tiles = g.ntiles > (int)blockIdx.x ? (g.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int Q = my_tiles * nchunk;   // K chunks this CTA walks (stage of chunk q: q mod S)
+    auto fail = [&]() {
+        if (!*abort_flag) atomicExch(g.err, TC_ERR_TIMEOUT);
+        *abort_flag = 1;
     };
 
-    float acc[TN];
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[j] = 0.f;
-    bool ok = true;
-    stage(0);
-    __syncthreads();
-    if (tid == 0) issue(0);
-    for (int c = 0; c < nchunk; ++c) {
-        if (c + 1 < nchunk) stage(c + 1);   // overlaps the MMAs of chunk c
-        const bool waited = mbar_wait_bounded(smem_u32(mbar), (uint32_t)(c & 1));
-        ok = __syncthreads_and(waited ? 1 : 0) != 0;
-        if (!ok) break;
-        if (c + 1 < nchunk && tid == 0) issue(c + 1);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t region = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((c & 1) * NREG * TN);
-        // sum the K-slices in FP32 (round to nearest): corrections first, then the main term
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const uint32_t rs = region + (uint32_t)((s ^ 1) * TN);   // order: corr0, main0, corr1, ...
-#pragma unroll
-            for (int j0 = 0; j0 < TN; j0 += 16) {
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15])
-                    : "r"(rs + (uint32_t)j0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j0 + j] += __uint_as_float(v[j]);
+    if (warp == TC_EPI_WARPS) {
+        // ---- TMA producer -------------------------------------------------------------------
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmBh) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmBl) : "memory");
+            int issued = 0, s = 0, c = 0, t = blockIdx.x;
+            uint32_t ph = 0;
+            for (int q = 0; q < Q; ++q) {
+                if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, g.wait_ns)) { fail(); break; }
+                const int mt = t / g.ntn, nt = t - mt * g.ntn;
+                const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
+                mbar_expect_tx(b_full + 8 * s, STAGE - ABYTES);   // A, Bt hi, Bt lo (A's lo buffer is ours)
+                tma_load_2d(sb, &tmA, c * TC_KC, mt * TC_BM, b_full + 8 * s);
+                tma_load_2d(sb + 2 * ABYTES, &tmBh, c * TC_KC, nt * BN, b_full + 8 * s);
+                tma_load_2d(sb + 2 * ABYTES + BBYTES, &tmBl, c * TC_KC, nt * BN, b_full + 8 * s);
+                issued = q + 1;
+                if (++s == S) { s = 0; ph ^= 1u; }
+                if (++c == nchunk) { c = 0; t += gridDim.x; }
             }
+            // our copies still in flight (only after an abort) finish before the CTA leaves
+            for (int q = issued - 1; q >= 0 && q >= issued - S; --q)
+                mbar_wait(b_full + 8 * (q % S), (uint32_t)((q / S) & 1), nullptr, g.wait_ns);
         }
-        // region (c & 1) is rewritten by the MMAs of chunk c + 2, issued after the next barrier
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    if (!ok) {
-        if (lane == 0) atomicExch(g.err, 1);
-        // give MMAs that may still be in flight a bounded chance to finish before freeing TMEM
-        for (int c = 0; c < 2; ++c) mbar_wait_bounded(smem_u32(mbar), 0u);
-    } else {
-        const long long m = m0 + warp * 32 + lane;
-        if (m < g.Mrows) {
-            const long long p = m / g.R;
-            const int r = (int)(m - p * g.R);
+        __syncwarp();
+    } else if (warp == TC_EPI_WARPS + 1) {
+        // ---- MMA issuer -----------------------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t idesc_full = idesc_tf32(TC_BM, BN), idesc_last = idesc_tf32(TC_BM, g.BNlast);
+            int grp = 0, committed = -1, s = 0, c = 0, cg = 0, t = blockIdx.x;
+            uint32_t ph = 0;
+            for (int q = 0; q < Q; ++q) {
+                const bool first = cg == 0;
+                const bool last = cg == g.group - 1 || c == nchunk - 1;
+                const int r = grp & 1;
+                if (first && !mbar_wait(b_rempty + 8 * r, (uint32_t)(((grp >> 1) & 1) ^ 1), abort_flag, g.wait_ns)) {
+                    fail();
+                    break;
+                }
+                if (!mbar_wait(b_conv + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t idesc = (t % g.ntn == g.ntn - 1) ? idesc_last : idesc_full;
+                const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
+                const uint32_t aH = sb, aL = sb + ABYTES, bH = sb + 2 * ABYTES, bL = bH + BBYTES;
+                const uint32_t d = tmem + (uint32_t)(r * BN);
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int n = n0 + j;
-                if (n < g.N) {
-                    float x = acc[j];
-                    if (g.lamN) {
-                        const float dd = g.lamN[n] + g.lamR[r] + g.cpl[p % g.cpl_mod];
-                        x = (dd != 0.f) ? x / dd : 0.f;
-                    }
-                    if (g.store == 0) g.C[m * g.N + n] = x;
-                    else g.C[(p * g.N + n) * g.R + r] = x;
-                    if (g.C2) {
-                        float w2 = -g.m2x[n] * g.m2y[r] * x;
-                        if (g.face2 && r == 0) w2 += g.face2[p * g.N + n];
-                        g.C2[m * g.N + n] = w2;
-                    }
+                for (int kk = 0; kk < TC_KC / 8; ++kk) {   // the small corrections first
+                    const uint32_t o = (uint32_t)(kk * 32);
+                    mma_tf32(d, sdesc_sw128(aL + o), sdesc_sw128(bH + o), idesc, (first && kk == 0) ? 0u : 1u);
+                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bL + o), idesc, 1u);
+                }
+#pragma unroll
+                for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                    const uint32_t o = (uint32_t)(kk * 32);
+                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bH + o), idesc, 1u);
+                }
+                mma_commit(b_empty + 8 * s);   // the stage is free once these MMAs have read it
+                committed = q;
+                if (last) {
+                    mma_commit(b_rfull + 8 * r);
+                    ++grp;
+                    cg = 0;
+                } else {
+                    ++cg;
+                }
+                if (++s == S) { s = 0; ph ^= 1u; }
+                if (++c == nchunk) { c = 0; cg = 0; t += gridDim.x; }
+            }
+            // MMAs in flight finish before the tensor memory is released
+            if (committed >= 0)
+                mbar_wait(b_empty + 8 * (committed % S), (uint32_t)((committed / S) & 1), nullptr, g.wait_ns);
+        }
+        __syncwarp();
+    } else {
+        // ---- split A, drain the accumulators, epilogue (warps 0-7) ----------------------------------
+        const int quarter = warp & 3, half = warp >> 2;
+        const int et = tid;   // 0..255
+        float acc[TC_MAXH];
+#pragma unroll
+        for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
+        int grp = 0, s = 0, c = -1, cg = -1, t = blockIdx.x;   // c, cg: chunk and place in group of q - 1
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int q = 0; q <= Q && ok; ++q) {
+            // split chunk q: hi in place, lo into the second A buffer (16 floats per thread)
+            if (q < Q) {
+                if (!mbar_wait(b_full + 8 * s, ph, abort_flag, g.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *sa = base + (size_t)s * STAGE;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t off = (uint32_t)(16 * (et + 256 * i));
+                    const float4 x = *(const float4 *)(sa + off);
+                    float4 h, l;
+                    h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+                    h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+                    h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+                    h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+                    *(float4 *)(sa + off) = h;
+                    *(float4 *)(sa + ABYTES + off) = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_conv + 8 * s);
+                if (++s == S) { s = 0; ph ^= 1u; }
+            }
+            // advance to chunk q - 1 of the schedule
+            if (q == 0) { c = 0; cg = 0; continue; }
+            const int cd = c, cgd = cg, td = t;
+            if (++c == nchunk) { c = 0; cg = 0; t += gridDim.x; }
+            else if (cgd == g.group - 1) cg = 0;
+            else ++cg;
+            // the group ending at chunk q - 1 (if it ends there): add it into the registers
+            if (!(cgd == g.group - 1 || cd == nchunk - 1)) continue;
+            const int r = grp & 1;
+            const int hbn = ((td % g.ntn == g.ntn - 1) ? g.BNlast : BN) >> 1;   // columns per thread
+            if (!mbar_wait(b_rfull + 8 * r, (uint32_t)((grp >> 1) & 1), abort_flag, g.wait_ns)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * BN + half * hbn);
+#pragma unroll
+            for (int j0 = 0; j0 < TC_MAXH; j0 += 16) {
+                if (j0 < hbn) {
+                    float v[16];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        if (j0 + 8 * u < hbn) tmem_ld8(ta + (uint32_t)(j0 + 8 * u), v + 8 * u);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j0 + j < hbn && j0 + j < TC_MAXH) acc[j0 + j] += v[j];
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_rempty + 8 * r);
+            ++grp;
+            if (cd != nchunk - 1) continue;
+            // ---- epilogue of tile td ------------------------------------------------------------
+            const int mt = td / g.ntn, nt = td - mt * g.ntn;
+            const int m = mt * TC_BM + quarter * 32 + lane;
+            const int nb = nt * BN + half * hbn;
+            if (m < g.M) {
+                const int p = m / g.R;
+                const int rr = m - p * g.R;
+                const float lr = g.lamN ? g.lamR[rr] + g.cpl[p % g.cpl_mod] : 0.f;
+                const float my = g.C2 ? g.m2y[rr] : 0.f;
+                // store 1: lanes hold consecutive rows r, so each column's stores are coalesced;
+                // store 0: a row's columns are contiguous (16-byte stores; ldc, nb multiples of 4)
+                float *cb = g.store == 1 ? g.C + ((long long)p * g.N + nb) * g.ldr + rr : g.C + (long long)m * g.ldc + nb;
+                float *c2b = g.C2 ? g.C2 + (long long)m * g.ldc + nb : nullptr;
+                const float *fb = (g.face2 && rr == 0) ? g.face2 + (long long)p * g.N + nb : nullptr;
+                const int ncol = min(hbn, g.N - nb);
+                // eight columns at a time; the empty asm keeps the loads of one group from being
+                // hoisted over the others (register pressure)
+#pragma unroll
+                for (int j0 = 0; j0 < TC_MAXH; j0 += 8) {
+                    if (j0 < ncol) {
+                        if (g.lamN) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (j0 + u < ncol) {
+                                    const float dd = g.lamN[nb + j0 + u] + lr;
+                                    acc[j0 + u] = (dd != 0.f) ? acc[j0 + u] / dd : 0.f;
+                                }
+                        }
+                        if (g.store == 1) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (j0 + u < ncol) cb[(long long)(j0 + u) * g.ldr] = acc[j0 + u];
+                        } else if (j0 + 8 <= ncol) {
+                            *(float4 *)(cb + j0) = make_float4(acc[j0], acc[j0 + 1], acc[j0 + 2], acc[j0 + 3]);
+                            *(float4 *)(cb + j0 + 4) = make_float4(acc[j0 + 4], acc[j0 + 5], acc[j0 + 6], acc[j0 + 7]);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (j0 + u < ncol) cb[j0 + u] = acc[j0 + u];
+                        }
+                        if (c2b) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (j0 + u < ncol) {
+                                    float w2 = -g.m2x[nb + j0 + u] * my * acc[j0 + u];
+                                    if (fb) w2 += fb[j0 + u];
+                                    c2b[j0 + u] = w2;
+                                }
+                        }
+                    }
+                    asm volatile("" ::: "memory");
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
         }
+        if (!ok) fail();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
     }
 }
 

@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True):
     L.pf_profile.argtypes = [c_void_p, c_int]
     L.pf_autotune.argtypes = [c_void_p, c_int, POINTER(c_int), dp]
     L.pf_set_variant.argtypes = [c_void_p, c_int, c_int, c_int]
+    L.pf_set_step.argtypes = [c_void_p, c_int, c_double]
+    L.pf_debug_tc_stall.argtypes = [c_void_p, ctypes.c_ulonglong]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
                                   POINTER(POINTER(c_double)), c_void_p, POINTER(c_void_p)]
@@ -257,6 +259,14 @@ class Solver:
     def set(self, mask: int, data: np.ndarray, reset_history: bool = False):
         data = _f64(data).ravel()
         _check(load().pf_set_fields(self._h, int(mask), _dp(data), data.size, int(reset_history)), self._h)
+
+    def set_step(self, nstep: int, t: float):
+        """Restart bookkeeping: step count (BDF order of the next step) and time."""
+        _check(load().pf_set_step(self._h, int(nstep), float(t)), self._h)
+
+    def debug_tc_stall(self, wait_ns: int):
+        """Test hook: the next tensor-core transform launch reports a time-out after wait_ns."""
+        _check(load().pf_debug_tc_stall(self._h, int(wait_ns)), self._h)
 
     def diagnostics(self) -> np.ndarray:
         out = np.zeros(8)

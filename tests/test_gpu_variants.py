@@ -37,10 +37,10 @@ def _direct(m, bcset, shift, f):
 
 
 @pytest.mark.parametrize("gemm,fuse_y", FP32_VARIANTS)
-@pytest.mark.parametrize("mesh", [(5, 4, 6), (16, 8, 8)])
+@pytest.mark.parametrize("mesh", [(6, 5, 6), (16, 8, 8)])
 @pytest.mark.parametrize("bcset", [native.PF_BCSET_V, native.PF_BCSET_U])
 def test_helmholtz_variant(gemm, fuse_y, mesh, bcset):
-    """A ragged plane (30 x 25 nodes) and the 128 x 65 plane of the 16 x 8, order-8 mesh, one
+    """A ragged plane (36 x 31 nodes) and the 128 x 65 plane of the 16 x 8, order-8 mesh, one
     Fourier mode pair, each variant within the FP32 bar of the assembled direct solve."""
     ex, ey, K = mesh
     wl = workloads.small3d(ex=ex, ey=ey, order=K, nz=4)
@@ -86,6 +86,13 @@ def test_set_variant_rejects_what_the_run_cannot_use():
         assert e.value.code == native.PF_EINVAL
     with pytest.raises(native.PfError):
         g64.set_variant(native.PF_GEMM_CLUSTER4)
+    # the tensor-core transforms need n_x % 4 == 0 (16-byte rows for TMA): 30 x 25 nodes cannot
+    odd = native.from_workload(workloads.small3d(ex=5, ey=4, order=6, nz=4), precision=native.PF_MIXED)
+    with pytest.raises(native.PfError) as e:
+        odd.set_variant(native.PF_GEMM_TC)
+    assert e.value.code == native.PF_EINVAL
+    odd.step(2)                                       # the default variant is a CUDA-core one there
+    odd.close()
     gs.set_variant(native.PF_GEMM_CLUSTER2)
     gs.set_variant(native.PF_GEMM_PLANE, tile=16)    # FP32 without tensor cores can take the plane solves
     gs.step(3)
@@ -161,7 +168,8 @@ def test_fp64_cuda_core_variants_agree_bit_for_bit(nz):
                 assert np.array_equal(f[k], ref[k]), (gemm, fuse_y, k)
 
 
-@pytest.mark.parametrize("gemm", [native.PF_GEMM_CLUSTER4, native.PF_GEMM_PLANE, native.PF_GEMM_PIPE32])
+@pytest.mark.parametrize("gemm", [native.PF_GEMM_TC, native.PF_GEMM_CLUSTER4, native.PF_GEMM_PLANE,
+                                  native.PF_GEMM_PIPE32])
 def test_variant_graph_replay_is_bit_identical(gemm):
     """A pinned variant replayed from the captured graphs gives the bits of eager launches."""
     torch = pytest.importorskip("torch")
