@@ -1,21 +1,29 @@
 #!/usr/bin/env python
-"""Throughput of the per-time-step path (Algorithm 2) on the 3D hybrid droplet workload.
+"""Throughput of the per-time-step path (Algorithm 2) on the 3D hybrid workloads.
 
-Workload (default): 16x8 spectral elements of order 8 times Nz = 64 Fourier planes,
-sphere of radius 0.25 on the bottom electrode (eps ratio 10, rho ratio 2, mu ratio 5),
-V = 2 / 0, dt = 5e-5.  One "step" = one full time step (V, E, psi, phi, P, u), all of it
-in the CUDA library through the C-ABI.  Metric: DOF-steps/s, DOF = real values of one
-scalar field = n_x n_y Nz = 532,480.
+Workload (default): layers3d, 32x16 spectral elements of order 10 times Nz = 256 Fourier planes
+(n_x n_y Nz = 13,189,120 real values per field; 6,646,080 complex coefficients), two stacked
+dielectric layers plus a drop (eps ratio 20, rho ratio 10, mu ratio 10), V = 2 / 0, dt = 5e-5.
+One "step" = one full time step (V, E, psi, phi, P, u), all of it in the CUDA library through the
+C-ABI.  Metric: DOF-steps/s, DOF = real values of one scalar field.  The mixed path is the value;
+the same line carries the FP64 path's rate and the mixed path's per-field error against it.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
 """
 from __future__ import annotations
 
+import os
+
+# the oracle legs run on one host core: BLAS and OpenMP pools are fixed before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ[_v] = "1"
+ORACLE_THREADS = 1
+
+
 import argparse
 import hashlib
 import json
 import math
-import os
 import subprocess
 import sys
 import tempfile
@@ -27,9 +35,6 @@ sys.path.insert(0, ROOT)
 METRIC = "DOF-steps/s at stated err vs FP64 oracle; time-to-equilibrium warm vs cold"
 UNIT = "DOF-steps/s"
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-FP64_FMA_PER_SM_CLK = 2        # FP64 rate of GB300 (about 1.25 TFLOP/s at 2.07 GHz)
 
 
 def peaks():
@@ -65,7 +70,6 @@ def oracle_sample(nsteps: int, warmup: int, name: str = "droplet3d"):
     """Steady-state BDF2 steps of the FP64 oracle on the workload's element mesh and physics
     (3D: with Nz = 8 planes; the oracle's sparse LU factorisations per mode make the full plane
     counts take minutes per step).  Returns (DOF-steps/s, seconds, description)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     import numpy as np
     from oracle.runner import solver_of
     wl = make_workload(name)
@@ -99,7 +103,8 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{args.workload} (oracle sample" +
                                                         (": Nz=8)" if args.workload != "patches2d" else ")")},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": ORACLE_THREADS, "host_cpus": os.cpu_count(),
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -206,6 +211,57 @@ def warmstart_arm(args):
     return 0
 
 
+# pinned FP64 transform variant per workload (what the autotuner picks on the GB300): cp.async 32x32
+# tiles with the fused y pair
+FP64_VARIANT = (4, 1)
+# timed oracle steps of the CPU baseline per workload (about 10-30 s of host work)
+ORACLE_STEPS = {"layers3d": 3, "droplet3d": 10, "electrode_array3d": 5, "patches2d": 10}
+
+
+def fp64_leg(args, wl, dof, prec, gemm_choice, fused_y, fft_tile, stream, flush, barrier):
+    """The FP64 path on the same workload: its rate (graph replays, L2 flushed between steps), and
+    the per-field relative L2 difference of the mixed path (the timed variant pinned) after
+    args.err_steps steps from the same initial state.  The FP64 path is itself held to 1e-11 of
+    the FP64 oracle by the parity tests."""
+    import numpy as np
+    import torch
+    from paper_2305_09020_gb300 import native
+    ALL_FIELDS = (native.PF_FIELD_V | native.PF_FIELD_E | native.PF_FIELD_PHI | native.PF_FIELD_PSI |
+                  native.PF_FIELD_P | native.PF_FIELD_U)
+    h64 = native.from_workload(wl, precision=native.PF_FP64, stream=stream.cuda_stream)
+    h64.set_variant(*FP64_VARIANT)
+    hm = native.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    hm.set_variant(gemm_choice, fuse_y=bool(fused_y), tile=fft_tile)
+    n = max(1, args.err_steps)
+    h64.step(n)
+    hm.step(n)
+    f64, fm = h64.get(ALL_FIELDS), hm.get(ALL_FIELDS)
+    hm.close()
+    err = {}
+    for k in f64:
+        nrm = float(np.linalg.norm(f64[k]))
+        if nrm > 0:
+            err[k] = float(np.linalg.norm(fm[k] - f64[k]) / nrm)
+    k64 = 3
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
+    barrier()
+    for k in range(k64):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        h64.step(1)
+        ev[k][1].record(stream)
+    barrier()
+    ms64 = sum(a.elapsed_time(b) for a, b in ev) / k64
+    h64.close()
+    return {"value": dof / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+            "variant": transform_kernel(*FP64_VARIANT) + " (FP64, pinned)",
+            "err_steps": n,
+            "mixed_rel_l2_vs_fp64": err,
+            "note": "relative L2 per field of the mixed path against the FP64 GPU path after err_steps steps "
+                    "from the same initial state; the FP64 path matches the FP64 oracle to 1e-11 (tests)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,10 +269,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_simt", "fp64"])
-    ap.add_argument("--workload", default="droplet3d", choices=sorted(WORKLOADS),
-                    help="droplet3d (the default bench line), or the electrode workloads")
+    ap.add_argument("--workload", default="layers3d", choices=sorted(WORKLOADS),
+                    help="layers3d (the default bench line), droplet3d, or the electrode workloads")
     ap.add_argument("--skip-extras", action="store_true", help="only the timed region (for profilers)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 rate and the error against it")
+    ap.add_argument("--err-steps", type=int, default=20, help="steps of the mixed-vs-FP64 error comparison")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the transform variant (a PF_GEMM_* code) instead of autotuning")
     ap.add_argument("--fused-y", type=int, default=0, help="with --variant: run the y pair fused (1) or not (0)")
@@ -305,6 +363,11 @@ def main():
         tot = sum(v[0] for v in cls.values())
         top = max(cls, key=lambda k: cls[k][0])
         pk, src = peaks()
+        props = torch.cuda.get_device_properties(dev)
+        mp = native.measure_peaks()          # this GPU, now: TF32 tensor, FP32 FFMA, FP64 DFMA
+        extras["measured_peaks"] = {**{k: round(v, 1) for k, v in mp.items()}, "sms": props.multi_processor_count,
+                                    "how": "pf_measure_peaks: tcgen05.mma kind::tf32 128x256x8 loop, one CTA per "
+                                           "SM; 8 independent FFMA / DFMA chains per thread; best of 5 launches"}
         per_launch_ms = cls[top][0] / max(1, cls[top][1] - launches1[top][1])
         roof = None
         if top == "gemm":
@@ -313,26 +376,26 @@ def main():
             nlaunch = cls["gemm"][1] - launches1["gemm"][1]
             achieved = flops / nlaunch / (per_launch_ms * 1e-3) / 1e12
             if prec == native.PF_MIXED and gemm_choice == 0:
-                # 3xTF32 on tcgen05: TF32 dense peak = measured bf16 peak x nominal TF32/BF16 (1.1/2.25)
-                peak = pk["bf16_tflops"] * (1.1 / 2.25)
-                roof = {"bound": "tensor", "kernel": "k_gemm_tc (3xTF32 fast-diagonalisation transforms)",
-                        "peak_source": f"{src} bf16 {pk['bf16_tflops']} TFLOP/s x 1.1/2.25 (TF32 dense); achieved "
-                                       "counts the FP32 GEMM flops, 3 TF32 MMAs are issued per useful product"}
+                # 3xTF32: three TF32 MMAs per FP32 product, so the FP32 GEMM's peak is a third of TF32's
+                peak = mp["tf32_tflops"] / 3.0
+                roof = {"bound": "tensor", "kernel": "k_gemm_tc (3xTF32 tcgen05 fast-diagonalisation transforms)",
+                        "peak_source": f"measured TF32 tensor peak {mp['tf32_tflops']:.0f} TFLOP/s / 3 (three TF32 "
+                                       "MMAs per FP32 product); achieved counts the FP32 GEMM flops 2MNK"}
             elif prec != native.PF_FP64:
-                peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                peak = mp["fp32_tflops"]
                 roof = {"bound": "alu", "kernel": transform_kernel(gemm_choice, fused_y) + " (FP32 SIMT transforms)",
-                        "peak_source": f"derived: {SM_COUNT} SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+                        "peak_source": "measured FP32 FFMA peak of this GPU"}
             else:
-                peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                peak = mp["fp64_tflops"]
                 roof = {"bound": "alu", "kernel": transform_kernel(gemm_choice, fused_y) + " (FP64 SIMT transforms)",
-                        "peak_source": f"derived: {SM_COUNT} SMs x 2 FP64 FMA/clk x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
-            traffic = (TRANSFORM_DRAM_BYTES_PER_LAUNCH.get((args.precision, gemm_choice, fused_y))
-                       if args.workload == "droplet3d" else None)
+                        "peak_source": "measured FP64 DFMA peak of this GPU"}
+            traffic = TRANSFORM_DRAM_BYTES_PER_LAUNCH.get((args.workload, args.precision, gemm_choice, fused_y))
             roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "launches_per_step": nlaunch / args.steps, "ms_per_launch": per_launch_ms,
                          "traffic": traffic,
                          "traffic_note": None if traffic is None else
                          "DRAM bytes per transform launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                         "mean of one solve's four launches on this workload, profiles/); algorithmic "
+                         "mean over one solve's launches on this workload, profiles/); algorithmic "
                          f"{transform_bytes_per_launch(nx, ny, nz, prec):.3e} B per launch"})
         else:
             roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -363,9 +426,13 @@ def main():
                          "h2d_bytes_per_step": int(hio.nbytes), "d2h_bytes_per_step": int(hio.nbytes + hvp.nbytes),
                          "steps": n_e2e, "what": "pf_set_fields(phi,u) + pf_step(1) + pf_get_fields(V,P) + "
                                                  "pf_get_fields(phi,u), pinned host buffers, no host-side copies"}
+        if prec != native.PF_FP64 and not args.no_fp64:
+            extras["fp64"] = fp64_leg(args, wl, dof, prec, gemm_choice, fused_y, fft_tile, stream, flush, barrier)
+            extras["fp64"]["mixed_speedup"] = (dof * args.steps / (ms * 1e-3)) / extras["fp64"]["value"]
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            val, secs, desc = oracle_sample(10, 2, args.workload)   # ~7 s of timed oracle work (droplet3d)
-            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+            val, secs, desc = oracle_sample(ORACLE_STEPS.get(args.workload, 10), 2, args.workload)
+            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": ORACLE_THREADS, "host_cpus": os.cpu_count(),
+                                      "kind": "oracle", "sample": desc}
     h.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -405,12 +405,25 @@ void pf_no_destroy(pf_no *h);
  * 2 * PF_STATIC_MAX_VALUES doubles (16 MiB) that every GPU loading this library holds
  * until exit.  nx*ny*nplanes > PF_STATIC_MAX_VALUES returns PF_EINVAL (message in
  * pf_last_error(NULL)).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Every call shares the array, so calls that overlap on the GPU (other streams,
- * other threads) race; each call fully overwrites the buffers before reading them. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of the process;
+ * make that first call before any stream capture.  Resetting the device (cudaDeviceReset) or
+ * calling from another context on that device after the first call is not supported: the kept
+ * address would belong to the old context.  Every call shares the array, so calls that overlap
+ * on the GPU (other streams, other threads) race; each call fully overwrites the buffers before
+ * reading them. */
 int pf_fdm_solve_static(int nx, int ny, int nplanes, const double *Sx, const double *SxT,
                         const double *lam_x, const double *Sy, const double *SyT, const double *lam_y,
                         const double *shift, const double *rhs, double *out, void *cuda_stream);
+
+/* ---- measured peaks ------------------------------------------------------------------- */
+
+/* Compute peaks of the current device, measured by microbenchmark kernels (the paper has no
+ * counterpart; these are the denominators of the benchmark's roofline fractions), in TFLOP/s:
+ * out[0] = TF32 tensor cores (tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, one CTA per SM),
+ * out[1] = FP32 FFMA on the CUDA cores, out[2] = FP64 DFMA.  Best of five timed launches each;
+ * synchronous, takes a few milliseconds.  PF_ECUDA without a device, PF_ETIMEOUT if the tensor-core
+ * loop's bounded wait gave up (messages in pf_last_error(NULL)). */
+int pf_measure_peaks(double out[3]);
 
 /* Release all device memory of the handle (NULL is a no-op). */
 void pf_destroy(pf_handle *h);

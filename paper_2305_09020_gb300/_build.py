@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libpf.so")
-SOURCES = ["pf_api.cu", "pf_setup.cpp", "pf_static.cu", "pf_no.cu"]
+SOURCES = ["pf_api.cu", "pf_setup.cpp", "pf_static.cu", "pf_no.cu", "pf_peaks.cu"]
 HEADERS = ["pf_kernels.cuh", "pf_tc.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -220,13 +220,13 @@ struct Engine {
     struct TcB {
         const T *key;
         float *hi, *lo;
-        int N, BN, BNlast, ntn, Npad, Kpad, stages, tmem_cols;
+        int N, BN, BNlast, ntn, Npad, Kpad, stages, tmem_cols, nr;
         size_t smem;
         CUtensorMap mh, ml;
     };
     std::vector<TcB> tcb;
     bool use_tc = false;
-    int tc_group = 1;                 // K chunks (of 32) per TMEM accumulation group
+    int tc_group = 1;                 // 8-wide K slices per TMEM accumulation group (1, 2 or 4)
     int tc_stall = 0;                 // test hook: the next tensor-core launch reports a time-out
     unsigned long long tc_wait_ns = 1000000000ull;   // bound of every wait (1 s)
     unsigned long long tc_wait_ns_next = 0;          // the test hook's bound
@@ -500,11 +500,11 @@ struct Engine {
         t.Npad = (t.ntn - 1) * t.BN + t.BNlast;
         t.Kpad = (n + pf::TC_KC - 1) / pf::TC_KC * pf::TC_KC;
         const size_t stage = (size_t)2 * pf::TC_BM * pf::TC_KC * 4 + (size_t)2 * t.BN * pf::TC_KC * 4;
-        const size_t fixed = 1024 + 256;   // alignment slack, barriers, TMEM slot, abort flag
+        const size_t fixed = 1024 + 512;   // alignment slack, barriers, TMEM slot, abort flag
         t.stages = (int)std::min<size_t>(4, (size_t)(227 * 1024 - fixed) / stage);
         t.smem = t.stages * stage + fixed;
-        t.tmem_cols = 32;
-        while (t.tmem_cols < 2 * t.BN) t.tmem_cols *= 2;
+        t.tmem_cols = 512;                 // the ring of accumulation regions: one CTA per SM
+        t.nr = std::min(pf::TC_MAXR, 512 / t.BN);
         std::vector<float> hi((size_t)t.Npad * t.Kpad, 0.f), lo((size_t)t.Npad * t.Kpad, 0.f);
         for (int r = 0; r < n; ++r)
             for (int k = 0; k < n; ++k) {
@@ -545,7 +545,7 @@ struct Engine {
         if (rows >= (1ll << 31)) throw CudaError{cudaErrorInvalidValue, "tensor-core transform with 2^31 rows"};
         a.M = (int)rows; a.N = tb->N; a.BN = tb->BN; a.BNlast = tb->BNlast; a.ntn = tb->ntn;
         a.nchunk = tb->Kpad / pf::TC_KC;
-        a.group = tc_group; a.stages = tb->stages; a.tmem_cols = tb->tmem_cols;
+        a.gs = tc_group; a.nr = tb->nr; a.stages = tb->stages; a.tmem_cols = tb->tmem_cols;
         a.ntiles = (int)((rows + pf::TC_BM - 1) / pf::TC_BM * tb->ntn);
         a.R = R; a.store = store; a.ldc = ldc; a.ldr = ldr;
         a.lamN = reinterpret_cast<const float *>(lamN);

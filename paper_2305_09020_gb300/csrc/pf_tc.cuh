@@ -14,9 +14,11 @@
 //               TMEM accumulators into FP32 registers and run the epilogue
 //   warp 9      one thread issues tcgen05.mma (M = 128, N = BN, K = 8) and commits to mbarriers
 // The tensor core's FP32 accumulation is not rounded to nearest, and the eigenvector sums cancel
-// heavily, so a long chain of MMAs in one accumulator loses digits.  Each group of `group` K chunks
-// therefore accumulates into its own TMEM region (two regions, ping-pong: the MMAs of group g+1
-// run while warps 0-7 add group g into registers with round-to-nearest), and within a group the
+// heavily, so a chain of MMAs in one accumulator loses digits (chunks of 32 in one region: phi of
+// the 2D droplet drifted 4x further from the oracle in 50 steps than with one region per slice).
+// Each group of `gs` 8-wide K slices (default 1) therefore accumulates into its own TMEM region,
+// taken from a ring of NR = 512 / BN regions: the MMAs of later groups run while warps 0-7 add the
+// finished groups into FP32 registers with round-to-nearest, in K order.  Within a slice the two
 // small correction products go first.  Every mbarrier wait is bounded (globaltimer); on time-out
 // the kernel records an error word, lets its own copies and MMAs finish (bounded), frees its
 // tensor memory and returns.
@@ -33,6 +35,7 @@ constexpr int TC_KC = 32;                           // K per stage: one 128-byte
 constexpr int TC_EPI_WARPS = 8;                     // two warpgroups, one per column half
 constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
 constexpr int TC_MAXH = 64;                         // accumulator columns per thread: BN <= 128
+constexpr int TC_MAXR = 8;                          // TMEM regions in the ring at most
 constexpr int TC_ERR_TIMEOUT = 1;                   // error word: a bounded wait gave up
 
 struct TcArgs {
@@ -42,7 +45,8 @@ struct TcArgs {
     int BNlast;               // width of the last column tile (multiple of 16, <= BN)
     int ntn;                  // column tiles
     int nchunk;               // K chunks of 32 (Kpad / 32)
-    int group;                // K chunks per TMEM accumulation group
+    int gs;                   // 8-wide K slices per TMEM accumulation group: 1, 2 or 4
+    int nr;                   // TMEM regions in the ring (nr BN <= tmem_cols, nr <= TC_MAXR)
     int stages;               // shared-memory stages
     int tmem_cols;            // allocated TMEM columns (power of two >= 2 BN)
     int ntiles;               // row tiles x column tiles
@@ -158,6 +162,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+#ifndef PF_TC_HELPERS_ONLY   // translation units that only need the helpers above
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
               const __grid_constant__ CUtensorMap tmBl, TcArgs g) {
@@ -168,10 +173,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t STAGE = 2 * ABYTES + 2 * BBYTES;
     uint64_t *bars = (uint64_t *)(base + (size_t)S * STAGE);
     // barriers: full[S] (TMA landed), conv[S] (A split), empty[S] (MMAs done with the stage),
-    // rfull[2] (a group's MMAs done), rempty[2] (a group drained), stall
+    // rfull[TC_MAXR] (a group's MMAs done), rempty[TC_MAXR] (a group drained), stall
+    const int NR = g.nr;
     const uint32_t b_full = smem_u32(bars), b_conv = b_full + 8 * S, b_empty = b_conv + 8 * S;
-    const uint32_t b_rfull = b_empty + 8 * S, b_rempty = b_rfull + 16, b_stall = b_rempty + 16;
-    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 5);
+    const uint32_t b_rfull = b_empty + 8 * S, b_rempty = b_rfull + 8 * TC_MAXR, b_stall = b_rempty + 8 * TC_MAXR;
+    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 2 * TC_MAXR + 1);
     volatile int *abort_flag = (volatile int *)(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(b_conv + 8 * s, TC_EPI_WARPS);
             mbar_init(b_empty + 8 * s, 1);
         }
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TC_MAXR; ++r) {
             mbar_init(b_rfull + 8 * r, 1);
             mbar_init(b_rempty + 8 * r, TC_EPI_WARPS);
         }
@@ -241,48 +247,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---- MMA issuer -----------------------------------------------------------------------
         if (lane == 0) {
             const uint32_t idesc_full = idesc_tf32(TC_BM, BN), idesc_last = idesc_tf32(TC_BM, g.BNlast);
-            int grp = 0, committed = -1, s = 0, c = 0, cg = 0, t = blockIdx.x;
+            int grp = 0, s = 0, c = 0, t = blockIdx.x;
             uint32_t ph = 0;
-            for (int q = 0; q < Q; ++q) {
-                const bool first = cg == 0;
-                const bool last = cg == g.group - 1 || c == nchunk - 1;
-                const int r = grp & 1;
-                if (first && !mbar_wait(b_rempty + 8 * r, (uint32_t)(((grp >> 1) & 1) ^ 1), abort_flag, g.wait_ns)) {
-                    fail();
-                    break;
-                }
+            bool ok = true;
+            for (int q = 0; q < Q && ok; ++q) {
                 if (!mbar_wait(b_conv + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t idesc = (t % g.ntn == g.ntn - 1) ? idesc_last : idesc_full;
                 const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
                 const uint32_t aH = sb, aL = sb + ABYTES, bH = sb + 2 * ABYTES, bL = bH + BBYTES;
-                const uint32_t d = tmem + (uint32_t)(r * BN);
-#pragma unroll
-                for (int kk = 0; kk < TC_KC / 8; ++kk) {   // the small corrections first
-                    const uint32_t o = (uint32_t)(kk * 32);
-                    mma_tf32(d, sdesc_sw128(aL + o), sdesc_sw128(bH + o), idesc, (first && kk == 0) ? 0u : 1u);
-                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bL + o), idesc, 1u);
-                }
-#pragma unroll
                 for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                    const bool first = kk % g.gs == 0, last = kk % g.gs == g.gs - 1;
+                    const int r = grp % NR;
+                    if (first) {
+                        if (!mbar_wait(b_rempty + 8 * r, (uint32_t)(((grp / NR) & 1) ^ 1), abort_flag, g.wait_ns)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    }
+                    const uint32_t d = tmem + (uint32_t)(r * BN);
                     const uint32_t o = (uint32_t)(kk * 32);
+                    // the two small correction products first, then the main term
+                    mma_tf32(d, sdesc_sw128(aL + o), sdesc_sw128(bH + o), idesc, first ? 0u : 1u);
+                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bL + o), idesc, 1u);
                     mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bH + o), idesc, 1u);
+                    if (last) {
+                        mma_commit(b_rfull + 8 * r);
+                        ++grp;
+                    }
                 }
+                if (!ok) break;
                 mma_commit(b_empty + 8 * s);   // the stage is free once these MMAs have read it
-                committed = q;
-                if (last) {
-                    mma_commit(b_rfull + 8 * r);
-                    ++grp;
-                    cg = 0;
-                } else {
-                    ++cg;
-                }
                 if (++s == S) { s = 0; ph ^= 1u; }
-                if (++c == nchunk) { c = 0; cg = 0; t += gridDim.x; }
+                if (++c == nchunk) { c = 0; t += gridDim.x; }
             }
-            // MMAs in flight finish before the tensor memory is released
-            if (committed >= 0)
-                mbar_wait(b_empty + 8 * (committed % S), (uint32_t)((committed / S) & 1), nullptr, g.wait_ns);
+            // every MMA issued (also after an abort) finishes before the tensor memory is released:
+            // one more commit, on the barrier the stall hook uses (idle on this path)
+            mma_commit(b_stall);
+            mbar_wait(b_stall, 0u, nullptr, g.wait_ns);
         }
         __syncwarp();
     } else {
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float acc[TC_MAXH];
 #pragma unroll
         for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
-        int grp = 0, s = 0, c = -1, cg = -1, t = blockIdx.x;   // c, cg: chunk and place in group of q - 1
+        int grp = 0, s = 0, c = 0, t = blockIdx.x;   // c, t: chunk and tile of q - 1
         uint32_t ph = 0;
         bool ok = true;
         for (int q = 0; q <= Q && ok; ++q) {
@@ -320,39 +324,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(b_conv + 8 * s);
                 if (++s == S) { s = 0; ph ^= 1u; }
             }
-            // advance to chunk q - 1 of the schedule
-            if (q == 0) { c = 0; cg = 0; continue; }
-            const int cd = c, cgd = cg, td = t;
-            if (++c == nchunk) { c = 0; cg = 0; t += gridDim.x; }
-            else if (cgd == g.group - 1) cg = 0;
-            else ++cg;
-            // the group ending at chunk q - 1 (if it ends there): add it into the registers
-            if (!(cgd == g.group - 1 || cd == nchunk - 1)) continue;
-            const int r = grp & 1;
+            if (q == 0) continue;
+            // the groups of chunk q - 1, in K order, into the registers
+            const int cd = c, td = t;
+            if (++c == nchunk) { c = 0; t += gridDim.x; }
             const int hbn = ((td % g.ntn == g.ntn - 1) ? g.BNlast : BN) >> 1;   // columns per thread
-            if (!mbar_wait(b_rfull + 8 * r, (uint32_t)((grp >> 1) & 1), abort_flag, g.wait_ns)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * BN + half * hbn);
-#pragma unroll
-            for (int j0 = 0; j0 < TC_MAXH; j0 += 16) {
-                if (j0 < hbn) {
-                    float v[16];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-                        if (j0 + 8 * u < hbn) tmem_ld8(ta + (uint32_t)(j0 + 8 * u), v + 8 * u);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (j0 + j < hbn && j0 + j < TC_MAXH) acc[j0 + j] += v[j];
+            for (int gi = 0; gi < (TC_KC / 8) / g.gs; ++gi) {
+                const int r = grp % NR;
+                if (!mbar_wait(b_rfull + 8 * r, (uint32_t)((grp / NR) & 1), abort_flag, g.wait_ns)) {
+                    ok = false;
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * BN + half * hbn);
+#pragma unroll
+                for (int j0 = 0; j0 < TC_MAXH; j0 += 16) {
+                    if (j0 < hbn) {
+                        float v[16];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+                            if (j0 + 8 * u < hbn) tmem_ld8(ta + (uint32_t)(j0 + 8 * u), v + 8 * u);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (j0 + j < hbn && j0 + j < TC_MAXH) acc[j0 + j] += v[j];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_rempty + 8 * r);
+                ++grp;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(b_rempty + 8 * r);
-            ++grp;
+            if (!ok) break;
             if (cd != nchunk - 1) continue;
             // ---- epilogue of tile td ------------------------------------------------------------
             const int mt = td / g.ntn, nt = td - mt * g.ntn;
@@ -419,5 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
     }
 }
+
+#endif  // PF_TC_HELPERS_ONLY
 
 }  // namespace pf

@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
     L.pf_autotune.argtypes = [c_void_p, c_int, POINTER(c_int), dp]
     L.pf_set_variant.argtypes = [c_void_p, c_int, c_int, c_int]
     L.pf_set_step.argtypes = [c_void_p, c_int, c_double]
+    L.pf_measure_peaks.argtypes = [POINTER(c_double)]
     L.pf_debug_tc_stall.argtypes = [c_void_p, ctypes.c_ulonglong]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
@@ -192,6 +193,13 @@ def fdm_solve_static(nx: int, ny: int, nplanes: int, Sx, SxT, lam_x, Sy, SyT, la
     ptrs = [c_void_p(int(p)) for p in (Sx, SxT, lam_x, Sy, SyT, lam_y, shift, rhs, out)]
     rc = L.pf_fdm_solve_static(int(nx), int(ny), int(nplanes), *ptrs, c_void_p(stream or 0))
     _check(rc, None)
+
+
+def measure_peaks() -> dict:
+    """Measured TF32 tensor, FP32 FFMA and FP64 DFMA peaks of the current device (TFLOP/s)."""
+    out = np.zeros(3)
+    _check(load().pf_measure_peaks(_dp(out)))
+    return {"tf32_tflops": float(out[0]), "fp32_tflops": float(out[1]), "fp64_tflops": float(out[2])}
 
 
 # ---- the time stepper -------------------------------------------------------------------------
