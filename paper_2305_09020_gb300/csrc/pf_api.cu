@@ -411,6 +411,16 @@ struct Engine {
         PSIH = mk<T>(N); Q2H = mk<T>(N); FACEH = mk<T>((size_t)nx * nz);
         if (fdm_y_smem() > 48 * 1024 && fdm_y_smem() <= 200 * 1024)
             raise_smem_limit((const void *)pf::k_fdm_y<T, 32, 8>, fdm_y_smem());
+        {   // z-transform kernels: opt in once, before any graph capture
+            const void *fns[] = {(const void *)pf::k_fwd<T, 0>, (const void *)pf::k_fwd<T, 4>,
+                                 (const void *)pf::k_fwd<T, 5>, (const void *)pf::k_fwd<T, 6>,
+                                 (const void *)pf::k_fwd<T, 7>, (const void *)pf::k_fwd<T, 8>,
+                                 (const void *)pf::k_inv<T, 0>, (const void *)pf::k_inv<T, 4>,
+                                 (const void *)pf::k_inv<T, 5>, (const void *)pf::k_inv<T, 6>,
+                                 (const void *)pf::k_inv<T, 7>, (const void *)pf::k_inv<T, 8>,
+                                 (const void *)pf::k_face_fft<T>};
+            for (const void *fn : fns) raise_smem_limit(fn, FFT_SMEM_LIMIT);
+        }
         if constexpr (sizeof(T) == 4) {
             if (plane_fits()) {   // opt in once, before any graph capture
                 const int cq = plane_cq();
@@ -638,8 +648,12 @@ struct Engine {
     // transform buffers of a non-power-of-two nz need a second (scratch) copy for the mixed radices
     bool nz_pow2() const { return (nz & (nz - 1)) == 0; }
     size_t fft_scratch(int pencils) const { return nz_pow2() ? 0 : (size_t)pencils * (nz + 1) * sizeof(cplx<T>); }
+    // shared memory of the z-transform pencils: 72 KB for 2^k planes (the FFT itself runs in
+    // registers for FP32 32..256 planes), half of it for the mixed radices (a scratch copy)
+    static constexpr int FFT_SMEM_BUDGET = 73728;
+    static constexpr size_t FFT_SMEM_LIMIT = 96 * 1024;   // raised once per kernel at set-up
     int fwd_tp() const {
-        int tp = (int)((nz_pow2() ? 24576 : 12288) / (sizeof(cplx<T>) * (nz + 1)));
+        int tp = (int)((nz_pow2() ? FFT_SMEM_BUDGET : FFT_SMEM_BUDGET / 2) / (sizeof(cplx<T>) * (nz + 1)));
         const int by_grid = tp_override > 0 ? tp_override : n2 / (4 * 152);
         if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;

@@ -559,14 +559,15 @@ __device__ __forceinline__ void fft_pencils(cplx<T> *buf, int ld, int npen, int 
     }
 }
 
-// The radix-2 DIT of fft_pencils for n = 2^LGZ = 32 or 64, one warp per pencil in registers:
-// lane l holds elements l and l + 32 (bit-reversed order as loaded).  A stage of half span h < 32
-// pairs lanes l and l ^ h (__shfl_xor), the stage of span 64 pairs the two elements of a lane; the
+// The radix-2 DIT of fft_pencils for n = 2^LGZ = 32 .. 256, one warp per pencil in registers:
+// lane l holds the E = n/32 elements l + 32 e (bit-reversed order as loaded).  A stage of half
+// span h < 32 pairs lanes l and l ^ h (__shfl_xor; the twiddle depends on l mod h only), a stage of
+// span h >= 32 pairs the lane's own elements e and e ^ (h/32) (twiddle of (l + 32 e) mod h); the
 // butterfly arithmetic is that of fft_pencils.  Called after the block barrier that completes the
 // buffer's loads; ends with a block barrier (the buffer is read by other threads next).
 template <typename T, int LGZ>
 __device__ __forceinline__ void fft_pencils_warp(cplx<T> *buf, int ld, int npen, const cplx<T> *tw, bool inverse) {
-    static_assert(LGZ == 5 || LGZ == 6, "one warp per pencil of 32 or 64 points");
+    static_assert(LGZ >= 5 && LGZ <= 8, "one warp per pencil of 32 to 256 points");
     constexpr int E = (1 << LGZ) / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int pen = warp; pen < npen; pen += nwarp) {
@@ -594,13 +595,19 @@ __device__ __forceinline__ void fft_pencils_warp(cplx<T> *buf, int ld, int npen,
                         v[e] = {pr.x - m.x, pr.y - m.y};
                     }
                 }
-            } else {   // span 64: elements lane and lane + 32 of this lane
-                cplx<T> w = tw[lane];
-                if (inverse) w.y = -w.y;
-                const cplx<T> m = cmul(v[E - 1], w);
-                const cplx<T> u = v[0];
-                v[0] = {u.x + m.x, u.y + m.y};
-                v[E - 1] = {u.x - m.x, u.y - m.y};
+            } else {   // span h >= 32: elements e and e + h/32 of this lane
+                const int hh = h >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & hh) == 0) {
+                        cplx<T> w = tw[(lane + 32 * (e & (hh - 1))) << (LGZ - s)];
+                        if (inverse) w.y = -w.y;
+                        const cplx<T> m = cmul(v[e + hh], w);
+                        const cplx<T> u = v[e];
+                        v[e] = {u.x + m.x, u.y + m.y};
+                        v[e + hh] = {u.x - m.x, u.y - m.y};
+                    }
+                }
             }
         }
 #pragma unroll
@@ -785,7 +792,7 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
         }
     }
     __syncthreads();
-    if constexpr ((LGZ == 5 || LGZ == 6) && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+    if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
         fft_pencils_warp<T, LGZ>(buf, ld, tp, stw, false);
     } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp, nz, stw, false);
@@ -911,7 +918,7 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
         }
     }
     __syncthreads();
-    if constexpr ((LGZ == 5 || LGZ == 6) && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+    if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
         fft_pencils_warp<T, LGZ>(buf, ld, tp * npair, stw, true);
     } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp * npair, nz, stw, true);
