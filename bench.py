@@ -55,6 +55,8 @@ WORKLOADS = {
                          "equilibrium system, pseudo-time step 2e-6",
     "patches2d": "patches2d: 16x4 elements order 8, four electrodes at -+0.5 on the wall, half-disc drop, "
                  "eps/rho/mu ratios 5/2/2, dt=1e-4",
+    "ensemble2d": "ensemble2d: 256 independent 2D runs (seed 20230515), meshes 4x2..24x12 elements, orders 4..10, "
+                  "V~U(0,3), eps ratio logU(2,20), drop radius U(0.15,0.35) on the wall, eta 0.02, dt 1e-4",
     "layers3d": "layers3d: 32x16 elements order 10 x Nz=256 planes, two stacked layers (fluid 1 below y=0.3) plus "
                 "a drop r=0.15 at (1,0.65,0.5), eta=0.005, eps/rho/mu ratios 20/10/10, V=2, dt=5e-5",
 }
@@ -73,6 +75,9 @@ def oracle_sample(nsteps: int, warmup: int, name: str = "droplet3d"):
     import numpy as np
     from oracle.runner import solver_of
     wl = make_workload(name)
+    if isinstance(wl, list):        # an ensemble: its first run stands for the sample
+        wl = wl[0]
+        name = name + " (first run)"
     if wl.mesh.nz > 1:
         wl.mesh.nz = 8
     sol = solver_of(wl, init=False)
@@ -262,6 +267,68 @@ def fp64_leg(args, wl, dof, prec, gemm_choice, fused_y, fft_tile, stream, flush,
                     "from the same initial state; the FP64 path matches the FP64 oracle to 1e-11 (tests)"}
 
 
+def ensemble_arm(args):
+    """The batched ensemble of 256 uneven 2D runs: DOF-steps/s of whole-ensemble steps (one CUDA
+    graph per step, groups on concurrent streams), then a bounded run to equilibrium with the
+    per-run exit on the device (max|u| < tol, checked after every step)."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2305_09020_gb300 import native
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    runs = workloads.ensemble2d()
+    prec = {"mixed": native.PF_MIXED, "mixed_simt": native.PF_MIXED_SIMT, "fp64": native.PF_FP64}[args.precision]
+    dofs = [(w.mesh.ex * w.mesh.order) * (w.mesh.ey * w.mesh.order + 1) for w in runs]
+    b = native.Batch(runs, precision=prec, stream=stream.cuda_stream)
+    ngroups = b.groups()[0]
+    b.step(args.warmup)
+    tune = b.autotune(steps=2)
+    b.step(2)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(0)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        b.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(c) for a, c in ev)
+    value = sum(dofs) * args.steps / (ms * 1e-3)
+    # bounded run to equilibrium: how many runs exit below tol within the cap, and the wall time
+    tol, cap = args.ens_tol, args.ens_cap
+    t0 = time.perf_counter()
+    steps = b.run_to_equilibrium(tol=tol, max_steps=b_steps_taken(args) + cap, check_every=200)
+    t_eq = time.perf_counter() - t0
+    b.close()
+    done = steps[steps > 0]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == native.PF_FP64 else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["ensemble2d"], "runs": len(runs), "groups": ngroups,
+                       "dof_per_step": int(sum(dofs)), "precision": args.precision,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "group_transform_ms": [round(float(x), 4) for x in tune]},
+            "clocks": clocks,
+            "run_to_equilibrium": {"tol": tol, "cap_steps": cap, "runs_below_tol": int(done.size),
+                                   "diverged": int((steps == -2).sum()), "wall_s": t_eq,
+                                   "exit_step_median": float(np.median(done)) if done.size else None,
+                                   "criterion": "max|u| < tol per run, checked on the device after every step; "
+                                                "a run that exits is frozen"}}
+    print(json.dumps(line))
+    return 0
+
+
+def b_steps_taken(args):
+    """Steps the ensemble has taken before its run to equilibrium: warm-up, autotuning
+    (6 variants x (2 + 1), rounded to even), 2 steady, the timed steps."""
+    return args.warmup + 18 + 2 + args.steps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,6 +342,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 rate and the error against it")
     ap.add_argument("--err-steps", type=int, default=20, help="steps of the mixed-vs-FP64 error comparison")
+    ap.add_argument("--ens-tol", type=float, default=1e-6, help="ensemble2d: equilibrium tolerance on max|u|")
+    ap.add_argument("--ens-cap", type=int, default=2000, help="ensemble2d: steps of the bounded run to equilibrium")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="override the workload's Fourier plane count (small profiler captures only)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the transform variant (a PF_GEMM_* code) instead of autotuning")
     ap.add_argument("--fused-y", type=int, default=0, help="with --variant: run the y pair fused (1) or not (0)")
@@ -292,6 +363,8 @@ def main():
         return warmstart_arm(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
+    if args.workload == "ensemble2d":
+        return ensemble_arm(args)
 
     import numpy as np
     import torch
@@ -309,6 +382,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     prec = {"mixed": native.PF_MIXED, "mixed_simt": native.PF_MIXED_SIMT, "fp64": native.PF_FP64}[args.precision]
     wl = make_workload(args.workload)
+    if args.nz > 0:
+        wl.mesh.nz = args.nz
     m = wl.mesh
     nx, ny, nz = m.ex * m.order, m.ey * m.order + 1, m.nz
     dof = nx * ny * nz
@@ -439,7 +514,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == native.PF_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload],
+            "config": {"workload": WORKLOADS[args.workload] + (f" (Nz overridden to {nz})" if args.nz > 0 else ""),
                        "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                        "fdm_gemm": {0: "tcgen05 3xTF32", 1: "whole solve per plane in shared memory (SIMT)",

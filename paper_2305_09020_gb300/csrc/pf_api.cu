@@ -212,6 +212,10 @@ struct Engine {
     bool indep = false;
     T *peps1 = nullptr, *peps2 = nullptr, *peps0 = nullptr, *pscale = nullptr, *pvb = nullptr, *pvt = nullptr;
     T *liftb = nullptr, *liftt = nullptr;
+    // ensembles: per-run exit on the device (pf_batch_run_to_equilibrium): run flags (0 = frozen),
+    // steps taken, exit step (-1 none, -2 not finite), and the tolerance (< 0: none)
+    int *active = nullptr, *run_count = nullptr, *steps_at = nullptr;
+    double *tol_dev = nullptr;
     double *red;
     int *dev_err;   // device error word (bounded waits)
     int cur = 0;
@@ -343,6 +347,8 @@ struct Engine {
                 if (s.vrow1 >= 0) lt[i] = s.Ky[(size_t)i * ny + (ny - 1)];
             }
             liftb = up(lb); liftt = up(lt);
+            active = mk<int>(nz); run_count = mk<int>(nz); steps_at = mk<int>(nz); tol_dev = mk<double>(1);
+            reset_exit(-1.0, 0);
         }
         {
             std::vector<cplx<T>> h(std::max(1, nz / 2));
@@ -599,11 +605,32 @@ struct Engine {
         for (void *q : allocs) cudaFree(q);
     }
 
+    // ensembles: every run active, no exit recorded, step counts `count`, tolerance tol (< 0: only
+    // non-finite runs stop)
+    void reset_exit(double tol, int count) {
+        std::vector<int> one(nz, 1), cnt(nz, count), none(nz, -1);
+        PF_CU(cudaMemcpyAsync(active, one.data(), nz * sizeof(int), cudaMemcpyHostToDevice, st));
+        PF_CU(cudaMemcpyAsync(run_count, cnt.data(), nz * sizeof(int), cudaMemcpyHostToDevice, st));
+        PF_CU(cudaMemcpyAsync(steps_at, none.data(), nz * sizeof(int), cudaMemcpyHostToDevice, st));
+        PF_CU(cudaMemcpyAsync(tol_dev, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
+        PF_CU(cudaStreamSynchronize(st));
+    }
+    // ensembles: per-run exit check after a step (the new level is in slot o, the old in slot n)
+    void batch_check(int n, int o) {
+        const bool eq = hs.model == PF_MODEL_EQUILIBRIUM;
+        prof->begin(PF_KC_OTHER, st);
+        pf::k_batch_check<T><<<nz, 256, 0, st>>>(eq ? phi[o] : u[0][o], eq ? nullptr : u[1][o], eq ? phi[n] : nullptr,
+                                                 1.0 / hs.dt, n2, tol_dev, active, run_count, steps_at);
+        check_launch();
+        prof->end(st);
+    }
+
     pf::Geo<T> geo() const {
         pf::Geo<T> g;
         g.ex = ex; g.ey = ey; g.K = K; g.p = p; g.nx = nx; g.ny = ny; g.n2 = n2; g.nz = nz;
         g.epb = epb();
         g.hx = hx; g.hy = hy; g.D = D; g.Dw = Dw; g.w = w; g.Mx = Mx; g.My = My;
+        g.active = active;
         return g;
     }
     pf::Phys<T> phys(int J) const {
@@ -662,10 +689,11 @@ struct Engine {
         while (p2 * 2 <= tp) p2 *= 2;
         return p2;
     }
-    // element kernels compiled for the orders of the timed workloads (8, 12), else generic
+    // element kernels compiled for the orders of the timed workloads (8, 10, 12), else generic
     template <typename F>
     void by_order(F f) {
         if (K == 8) f(std::integral_constant<int, 8>{});
+        else if (K == 10) f(std::integral_constant<int, 10>{});
         else if (K == 12) f(std::integral_constant<int, 12>{});
         else f(std::integral_constant<int, 0>{});
     }
@@ -673,7 +701,7 @@ struct Engine {
 
     void gemm(const T *A, const T *B, T *C, long long Mrows, int Ncol, int R, int store, const T *lamN,
               const T *lamR, const T *cpl, int cpl_mod, T *C2 = nullptr, const T *face2 = nullptr) {
-        pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod, C2, Mx, My, face2};
+        pf::GemmArgs<T> g{A, B, C, Mrows, Ncol, R, store, lamN, lamR, cpl, cpl_mod, C2, Mx, My, face2, active, nz};
         constexpr int BK = sizeof(T) == 8 ? 8 : 16;
         if (simt_tile >= 3 && simt_tile <= 5) {   // cp.async pipelines: 64x64, 32x32, 32x64 tiles
             constexpr int VWE = 16 / (int)sizeof(T);
@@ -771,7 +799,7 @@ struct Engine {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             PF_CU(cudaLaunchKernelEx(&cfg, pf::k_fdm_cluster<CL, CQ>, rhs, out, nx, ny, Sx, Sy[bcset], Lx, Ly[bcset],
-                                     sh, nz, c2, Mx, My, face));
+                                     sh, nz, c2, Mx, My, face, (const int *)active));
         }
     }
     template <int CL>
@@ -797,7 +825,7 @@ struct Engine {
         if constexpr (sizeof(T) == 4) {
             const unsigned threads = 32u * (unsigned)(pf::fdm_plane_nyp(ny) / 8);
             pf::k_fdm_plane<CQ><<<(unsigned)P, threads, fdm_plane_smem(), st>>>(
-                rhs, out, nx, ny, Sx, Sy[bcset], Lx, Ly[bcset], sh, nz, c2, Mx, My, face);
+                rhs, out, nx, ny, Sx, Sy[bcset], Lx, Ly[bcset], sh, nz, c2, Mx, My, face, active);
         }
     }
 
@@ -833,7 +861,7 @@ struct Engine {
             const int threads = ((BM * ((ny + CG - 1) / CG) + 31) / 32) * 32;
             prof->begin(PF_KC_GEMM, st);
             pf::k_fdm_y<T, BM, CG><<<(unsigned)((P * nx + BM - 1) / BM), threads, fdm_y_smem(), st>>>(
-                W1, Sy[bcset], SyT[bcset], W2, P * nx, ny, nx, Ly[bcset], Lx, sh, nz);
+                W1, Sy[bcset], SyT[bcset], W2, P * nx, ny, nx, Ly[bcset], Lx, sh, nz, active);
             check_launch();
             prof->end(st);
             gemm(W2, SxT, out, P * ny, nx, ny, 0, nullptr, nullptr, nullptr, 1, minus_m_out, face);
@@ -902,10 +930,10 @@ struct Engine {
         check_launch();
         prof->end(st);
     }
-    void inv_indep(const T *Y, T *out, bool dirichlet_v, bool phi_variant, double alpha, int ncomp = 1) {
+    void inv_indep(const T *Y, T *out, T *cur_level, bool dirichlet_v, bool phi_variant, double alpha, int ncomp = 1) {
         pf::IndepInv<T> a{};
         a.cs_y = N; a.cs_out = N;
-        a.Y = Y; a.out = out;
+        a.Y = Y; a.out = out; a.cur = cur_level;
         a.drow0 = dirichlet_v ? hs.vrow0 : -1; a.drow1 = dirichlet_v ? hs.vrow1 : -1;
         a.v0_p = pvb; a.v1_p = pvt;
         if (phi_variant) {
@@ -935,7 +963,7 @@ struct Engine {
         else fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0 / hs.eps0, liftV, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_V, shV, nz);
         if (hs.patch) patch_correction();
-        if (indep) inv_indep(OUT, Vout, true, false, 0.0);
+        if (indep) inv_indep(OUT, Vout, Vout == V[0] ? V[1] : V[0], true, false, 0.0);
         else if (hs.patch) inv(OUT, Vout, Ezout, -1, 0.0, hs.vrow1, hs.v1);
         else inv(OUT, Vout, Ezout, hs.vrow0, hs.v0, hs.vrow1, hs.v1);
     }
@@ -1015,9 +1043,10 @@ struct Engine {
         fdm(RHS, PSIH, PF_BCSET_NN, shPsi[J - 1], nz, rhs_phi, faceh);
         // phi^{n+1}
         fdm(rhs_phi, OUT, PF_BCSET_NN, shPhi[J - 1], nz);
-        if (indep) inv_indep(OUT, phi[o], false, true, al);
+        if (indep) inv_indep(OUT, phi[o], phi[n], false, true, al);
         else inv_phi(al, phi[o], dzphi[o]);
         if (hs.model == PF_MODEL_EQUILIBRIUM) {   // Sec. 2.4: u = 0, no pressure or velocity step
+            if (indep) batch_check(n, o);
             cur = o;
             return;
         }
@@ -1041,7 +1070,7 @@ struct Engine {
         if (indep) fwd_indep(LA, nullptr, nullptr, false, RHS, nullptr);
         else fwd(LA, 1, d3 ? LB : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr);
         fdm(RHS, OUT, PF_BCSET_P, shP, nz);
-        if (indep) inv_indep(OUT, P[o], false, false, 0.0);
+        if (indep) inv_indep(OUT, P[o], P[n], false, false, 0.0);
         else inv(OUT, P[o], dzP[o], -1, 0.0, -1, 0.0);
         // u^{n+1}
         prof->begin(PF_KC_UGRADP, st);
@@ -1056,8 +1085,9 @@ struct Engine {
         if (indep) fwd_indep(LAU[0], nullptr, nullptr, false, RHS, nullptr, dc);
         else fwd(LAU[0], 1, d3 ? LBU[0] : nullptr, 1, 0, 1.0, nullptr, RHS, nullptr, dc);
         fdm(RHS, OUT, PF_BCSET_U, shU[J - 1], dc * nz);
-        if (indep) inv_indep(OUT, u[0][o], false, false, 0.0, dc);
+        if (indep) inv_indep(OUT, u[0][o], u[0][n], false, false, 0.0, dc);
         else inv(OUT, u[0][o], dzu[0][o], -1, 0.0, -1, 0.0, dc);
+        if (indep) batch_check(n, o);
         cur = o;
     }
 
@@ -1946,10 +1976,13 @@ struct pf_batch {
         std::unique_ptr<Engine<float>> e32;
         std::vector<int> runs;
         int v_iters = 0;
+        cudaStream_t gst = nullptr;        // the group's own stream: groups run concurrently
+        cudaEvent_t joined = nullptr;      // recorded on gst at the end of a step
     };
     std::vector<std::unique_ptr<Group>> groups;
     std::vector<std::pair<int, int>> where;   // run -> (group, plane)
     cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr;                // recorded on st before a step
     long long nstep = 0;
     int bdf = 2;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1958,7 +1991,16 @@ struct pf_batch {
     ~pf_batch() {
         for (int c = 0; c < 2; ++c)
             if (graph[c]) cudaGraphExecDestroy(graph[c]);
+        for (auto &g : groups)
+            if (g->gst) cudaStreamSynchronize(g->gst);
+        groups.clear();   // engines first, then their streams and events
+        for (auto e : streams_events) {
+            if (e.first) cudaStreamDestroy(e.first);
+            if (e.second) cudaEventDestroy(e.second);
+        }
+        if (fork) cudaEventDestroy(fork);
     }
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> streams_events;
 };
 
 namespace {
@@ -1992,10 +2034,22 @@ void batch_invalidate_graphs(pf_batch *b) {
         }
 }
 
+// one step of every group, each on its own stream, between a fork on the ensemble's stream and a
+// join back into it (in a capture the group streams join the graph as concurrent branches)
+void batch_step_groups(pf_batch *b, int J) {
+    PF_CU(cudaEventRecord(b->fork, b->st));
+    for (auto &g : b->groups) {
+        PF_CU(cudaStreamWaitEvent(g->gst, b->fork, 0));
+        for_engine(*g, [&](auto &E) { E.step(J); });
+        PF_CU(cudaEventRecord(g->joined, g->gst));
+        PF_CU(cudaStreamWaitEvent(b->st, g->joined, 0));
+    }
+}
+
 void batch_step_once(pf_batch *b) {
     const int J = (b->nstep == 0 || b->bdf == 1) ? 1 : 2;
     if (J == 1 || b->st == nullptr) {
-        for (auto &g : b->groups) for_engine(*g, [&](auto &E) { E.step(J); });
+        batch_step_groups(b, J);
     } else {
         int c = 0;
         for_engine(*b->groups[0], [&](auto &E) { c = E.cur; });
@@ -2005,7 +2059,7 @@ void batch_step_once(pf_batch *b) {
             for (auto &g : b->groups) before.emplace_back(g->prof.launches, g->prof.launches + PF_KC_COUNT);
             PF_CU(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
             try {
-                for (auto &g : b->groups) for_engine(*g, [&](auto &E) { E.step(2); });
+                batch_step_groups(b, 2);
             } catch (...) {
                 cudaStreamEndCapture(b->st, &gr);
                 if (gr) cudaGraphDestroy(gr);
@@ -2079,15 +2133,19 @@ extern "C" int pf_batch_create(int nrun, const pf_mesh *meshes, const pf_fluid *
         g.hs.bvt.push_back(setups[r].v1);
     }
     try {
+        PF_CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
         for (auto &gp : b->groups) {
             auto &g = *gp;
+            PF_CU(cudaStreamCreateWithFlags(&g.gst, cudaStreamNonBlocking));
+            PF_CU(cudaEventCreateWithFlags(&g.joined, cudaEventDisableTiming));
+            b->streams_events.push_back({g.gst, g.joined});
             g.hs.batch = (int)g.runs.size();
             build_setup(g.hs);
             const size_t n2 = (size_t)g.hs.nx * g.hs.ny;
             std::vector<double> phi(n2 * g.runs.size());
             for (size_t i = 0; i < g.runs.size(); ++i) std::copy(phi0[g.runs[i]], phi0[g.runs[i]] + n2, phi.begin() + i * n2);
             std::string err;
-            const int rc = build_engines(g.hs, phi.data(), nullptr, b->st, &g.prof, g.e64, g.e32, g.v_iters, err);
+            const int rc = build_engines(g.hs, phi.data(), nullptr, g.gst, &g.prof, g.e64, g.e32, g.v_iters, err);
             if (rc != PF_OK) return fail(nullptr, rc, err);
         }
     } catch (const CudaError &e) {
@@ -2139,28 +2197,37 @@ extern "C" int pf_batch_umax(pf_batch *b, double *umax, double *mass) {
 }
 
 extern "C" int pf_batch_run_to_equilibrium(pf_batch *b, double tol, int max_steps, int check_every, int *steps_out) {
-    if (!b || !steps_out || check_every < 1 || max_steps < 0) return PF_EINVAL;
+    if (!b || !steps_out || check_every < 1 || max_steps < 0 || !(tol >= 0.0)) return PF_EINVAL;
     const int nrun = (int)b->where.size();
-    std::vector<double> um(nrun);
-    for (int r = 0; r < nrun; ++r) steps_out[r] = -1;
-    int left = nrun;
-    while (left > 0 && b->nstep < max_steps) {
-        const int n = (int)std::min<long long>(check_every, max_steps - b->nstep);
-        int rc = pf_batch_step(b, n);
-        if (rc != PF_OK) return rc;
-        rc = pf_batch_umax(b, um.data(), nullptr);
-        if (rc != PF_OK) return rc;
-        for (int r = 0; r < nrun; ++r) {
-            if (steps_out[r] != -1) continue;
-            if (!(um[r] == um[r]) || std::isinf(um[r])) {   // runs are independent: record and go on
-                steps_out[r] = -2;
-                --left;
-            } else if (um[r] < tol) {
-                steps_out[r] = (int)b->nstep;
-                --left;
-            }
+    try {
+        // every run active, its step count the ensemble's; each step ends with the device check
+        for (auto &g : b->groups) for_engine(*g, [&](auto &E) { E.reset_exit(tol, (int)b->nstep); });
+        while (b->nstep < max_steps) {
+            const int n = (int)std::min<long long>(check_every, max_steps - b->nstep);
+            const int rc = pf_batch_step(b, n);
+            if (rc != PF_OK) return rc;
+            bool any = false;   // the host only decides when to stop launching
+            for (auto &g : b->groups)
+                for_engine(*g, [&](auto &E) {
+                    std::vector<int> act(E.nz);
+                    PF_CU(cudaMemcpyAsync(act.data(), E.active, E.nz * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+                    PF_CU(cudaStreamSynchronize(E.st));
+                    for (int v : act) any = any || v;
+                });
+            if (!any) break;
         }
+        for (auto &g : b->groups)
+            for_engine(*g, [&](auto &E) {
+                std::vector<int> at(E.nz);
+                PF_CU(cudaMemcpyAsync(at.data(), E.steps_at, E.nz * sizeof(int), cudaMemcpyDeviceToHost, E.st));
+                PF_CU(cudaStreamSynchronize(E.st));
+                for (size_t i = 0; i < g->runs.size(); ++i) steps_out[g->runs[i]] = at[i];
+                E.reset_exit(-1.0, (int)b->nstep);   // later pf_batch_step calls advance every run again
+            });
+    } catch (const CudaError &e) {
+        return batch_fail(b, PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
     }
+    (void)nrun;
     return PF_OK;
 }
 

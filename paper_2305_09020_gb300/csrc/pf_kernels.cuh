@@ -51,7 +51,14 @@ struct Geo {
     const T *Dw;        // Dw[a*p+c] = w_a D[a*p+c]
     const T *w;         // GLL weights
     const T *Mx, *My;   // assembled 1D masses
+    const int *active;  // ensembles: per-plane (run) flag, 0 = frozen (its step is skipped); else null
 };
+
+// a frozen ensemble run (blockIdx.y = plane): its element and transform work is skipped
+template <typename T>
+__device__ __forceinline__ bool plane_frozen(const Geo<T> &G) {
+    return G.active && !G.active[blockIdx.y];
+}
 
 template <typename T>
 struct Phys {
@@ -198,6 +205,7 @@ template <typename T, int KC = 0>
 __global__ void k_potential(Geo<T> G_, Phys<T> q_, const T *__restrict__ phin, const T *__restrict__ phio,
                             const T *__restrict__ Vn, const T *__restrict__ Vo, const T *__restrict__ Ezn,
                             const T *__restrict__ Ezo, T *__restrict__ A, T *__restrict__ B) {
+    if (plane_frozen(G_)) return;
     const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 3)
     const Phys<T> q = plane_phys(q_);
@@ -293,6 +301,7 @@ __global__ void k_chem(Geo<T> G_, Phys<T> q_, const T *__restrict__ phin, const 
                        const T *__restrict__ uyo, const T *__restrict__ uzn, const T *__restrict__ uzo,
                        const T *__restrict__ Ex, const T *__restrict__ Ey, const T *__restrict__ Ez,
                        T *__restrict__ A, T *__restrict__ Q2n, T *__restrict__ faceU) {
+    if (plane_frozen(G_)) return;
     const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 4)
     const Phys<T> q = plane_phys(q_);
@@ -356,6 +365,7 @@ struct MomOut {
 
 template <typename T, int KC = 0>
 __global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
+    if (plane_frozen(G_)) return;
     const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 12)
     const Phys<T> q = plane_phys(q_);
@@ -485,6 +495,7 @@ __global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
 template <typename T, int KC = 0>
 __global__ void k_ugradp(Geo<T> G_, Phys<T> q, const T *__restrict__ P, T *__restrict__ AUx,
                          T *__restrict__ AUy, T *__restrict__ BUz) {
+    if (plane_frozen(G_)) return;
     const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 1)
     T *sPv = sF;
@@ -956,7 +967,7 @@ struct IndepFwd {
 template <typename T>
 __global__ void k_fwd_indep(Geo<T> G, IndepFwd<T> a) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= G.n2) return;
+    if (q >= G.n2 || plane_frozen(G)) return;
     const int p = blockIdx.y;
     int s[4];
     dss_sources(G, q, s);
@@ -979,6 +990,7 @@ struct IndepInv {
     int drow0, drow1;         // Dirichlet rows (-1: none) receiving v0_p / v1_p
     const T *v0_p, *v1_p;
     T *out;
+    T *cur;                   // level n of the same field (frozen runs swap it with out)
     // phi variant
     const T *psi, *Q2n;
     T alpha, S_eta2;
@@ -991,6 +1003,15 @@ __global__ void k_inv_indep(Geo<T> G, IndepInv<T> a) {
     if (q >= G.n2) return;
     const int p = blockIdx.y;
     const long long gi = (long long)p * G.n2 + q;
+    if (plane_frozen(G)) {
+        // the run has stopped: exchange its two history levels, so that after the slots change
+        // roles it holds the same level n and n - 1 as before this step
+        const long long o = blockIdx.z * a.cs_out + gi;
+        const T t = a.out[o];
+        a.out[o] = a.cur[o];
+        a.cur[o] = t;
+        return;
+    }
     T x = a.Y[blockIdx.z * a.cs_y + gi];
     const int i = q / G.nx;
     if (a.drow0 >= 0 && i == a.drow0) x += a.v0_p[p];
@@ -1008,7 +1029,7 @@ __global__ void k_inv_indep(Geo<T> G, IndepInv<T> a) {
 template <typename T>
 __global__ void k_face_indep(Geo<T> G, const T *__restrict__ face, T *__restrict__ out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= G.nx) return;
+    if (j >= G.nx || plane_frozen(G)) return;
     const int p = blockIdx.y, K = G.K, pp = G.p;
     const long long base = (long long)p * G.ex;
     T v;
@@ -1047,6 +1068,44 @@ __global__ void k_reduce_planes(const T *__restrict__ x, const T *__restrict__ y
         __syncthreads();
     }
     if (threadIdx.x == 0) out[p] = sm[0];
+}
+
+// Per-run exit of an ensemble (one block per run, after the run's step): the run's FP64 max |u|
+// (equilibrium system: max |phi^{n+1} - phi^n| / dt) against *tol; a run that falls below it, or
+// whose value is not finite, is frozen (active = 0) and its step count recorded in steps_at
+// (-2 when not finite).  count[p] counts the steps the run has taken.
+template <typename T>
+__global__ void k_batch_check(const T *__restrict__ a0, const T *__restrict__ a1, const T *__restrict__ phin,
+                              double inv_dt, int n2, const double *__restrict__ tol, int *__restrict__ active,
+                              int *__restrict__ count, int *__restrict__ steps_at) {
+    const int p = blockIdx.x;
+    if (!active[p]) return;
+    __shared__ double sm[256];
+    const long long off = (long long)p * n2;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        double v;
+        if (phin) v = fabs((double)a0[off + i] - (double)phin[off + i]) * inv_dt;
+        else v = fmax(fabs((double)a0[off + i]), fabs((double)a1[off + i]));
+        if (!(v == v) || isinf(v)) v = INFINITY;   // not finite: stops the run
+        m = fmax(m, v);
+    }
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int c = ++count[p];
+        if (isinf(sm[0])) {
+            active[p] = 0;
+            steps_at[p] = -2;
+        } else if (sm[0] < *tol) {
+            active[p] = 0;
+            steps_at[p] = c;
+        }
+    }
 }
 
 // z-FFT of the wall face slots (direct stiffness summation along x first)
@@ -1108,10 +1167,23 @@ struct GemmArgs {
     // the phi right-hand side -M psi (+ wall term) written by the psi solve's last transform
     T *C2;
     const T *m2x, *m2y, *face2;
+    const int *active;   // ensembles: per-run flags (0 = frozen), run = plane % amod; null otherwise
+    int amod;
 };
+
+// ensembles: true when every row of the tile [m0, m0 + BM) belongs to a frozen run (plane = m / R)
+template <typename T>
+__device__ __forceinline__ bool tile_frozen(const GemmArgs<T> &g, long long m0, int BM) {
+    if (!g.active) return false;
+    const long long p1 = (min(m0 + BM, g.Mrows) - 1) / g.R;
+    for (long long p = m0 / g.R; p <= p1; ++p)
+        if (g.active[p % g.amod]) return false;
+    return true;
+}
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(GemmArgs<T> g) {
+    if (tile_frozen(g, (long long)blockIdx.y * BM, BM)) return;
     constexpr int NTH = (BM / TM) * (BN / TN);
     constexpr int LA = BM * BK / NTH;   // A elements staged per thread per k tile
     constexpr int LB = BK * BN / NTH;
@@ -1238,6 +1310,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, int STAGES, bool VEC>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_cp(GemmArgs<T> g) {
+    if (tile_frozen(g, (long long)blockIdx.y * BM, BM)) return;
     constexpr int NTH = (BM / TM) * (BN / TN);
     constexpr int VW = VEC ? 16 / (int)sizeof(T) : 1;   // elements per copy
     constexpr int PA = 16 / (int)sizeof(T);             // A row padding (keeps rows 16-byte aligned)
@@ -1371,7 +1444,14 @@ __device__ __forceinline__ void block_stage(int n, Src src, Dst dst) {
 template <typename T, int BM, int CG>
 __global__ void k_fdm_y(const T *__restrict__ A, const T *__restrict__ Sy, const T *__restrict__ SyT,
                         T *__restrict__ C, long long Mrows, int ny, int R, const T *__restrict__ lamN,
-                        const T *__restrict__ lamR, const T *__restrict__ cpl, int cpl_mod) {
+                        const T *__restrict__ lamR, const T *__restrict__ cpl, int cpl_mod,
+                        const int *__restrict__ active) {
+    if (active) {   // ensembles: skip a block whose rows all belong to frozen runs
+        const long long b0 = (long long)blockIdx.x * BM, b1 = (min(b0 + BM, Mrows) - 1) / R;
+        bool any = false;
+        for (long long p = b0 / R; p <= b1 && !any; ++p) any = active[p % cpl_mod] != 0;
+        if (!any) return;
+    }
     extern __shared__ unsigned char pf_smem_raw[];
     T *sS = reinterpret_cast<T *>(pf_smem_raw);    // ny x ny
     T *sST = sS + ny * ny;                         // ny x ny
@@ -1466,7 +1546,9 @@ __global__ void __launch_bounds__(512) k_fdm_plane(const float *__restrict__ rhs
                                                      const float *__restrict__ Ly, const float *__restrict__ cpl,
                                                      int cpl_mod, float *__restrict__ C2,
                                                      const float *__restrict__ Mx, const float *__restrict__ My,
-                                                     const float *__restrict__ face2) {
+                                                     const float *__restrict__ face2,
+                                                     const int *__restrict__ run_active) {
+    if (run_active && !run_active[blockIdx.x % cpl_mod]) return;   // ensembles: a frozen run
     constexpr int NXP = 32 * CQ, RW = 8;
     extern __shared__ __align__(16) unsigned char pf_smem_raw[];
     const int nyp = fdm_plane_nyp(ny);
@@ -1616,7 +1698,9 @@ __global__ void __launch_bounds__(256) k_fdm_cluster(const float *__restrict__ r
                                                       const float *__restrict__ Ly, const float *__restrict__ cpl,
                                                       int cpl_mod, float *__restrict__ C2,
                                                       const float *__restrict__ Mx, const float *__restrict__ My,
-                                                      const float *__restrict__ face2) {
+                                                      const float *__restrict__ face2,
+                                                      const int *__restrict__ run_active) {
+    if (run_active && !run_active[(blockIdx.x / CL) % cpl_mod]) return;   // ensembles: a frozen run (whole cluster)
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     constexpr int NXP = 32 * CQ, NW = 8, KB = 16;

@@ -84,9 +84,50 @@ def test_batch_run_to_equilibrium_reports_steps():
     runs = uneven_runs()
     b = native.Batch(runs, precision=native.PF_FP64)
     steps = b.run_to_equilibrium(tol=1e30, max_steps=10, check_every=4)
-    assert np.all(steps == 4)
+    assert np.all(steps == 1)            # the exit is checked on the device after every step
     steps = b.run_to_equilibrium(tol=0.0, max_steps=10, check_every=4)   # never below 0
     assert np.all(steps == -1)
+    b.close()
+
+
+def test_per_run_exit_is_exact_and_freezes_the_run():
+    """Equilibrium system (pseudo-time rate max|phi^{n+1} - phi^n| / dt, which decays): each run of
+    an uneven ensemble stops at the first step its own rate falls below the tolerance, found on
+    the device whatever check_every is, and its fields stay those of that step while the other runs
+    go on.  The reference is each run alone on a handle of its own."""
+    runs = uneven_runs()
+    for w in runs:
+        w.scheme.equilibrium = True
+    nmax = 40
+    rates, states = [], []
+    for wl in runs:
+        h = native.from_workload(wl, precision=native.PF_FP64)
+        r, st = [], []
+        for _ in range(nmax):
+            h.step(1)
+            r.append(h.diagnostics()[6])
+            st.append(h.get(ALL))
+        h.close()
+        rates.append(np.array(r))
+        states.append(st)
+    # a tolerance halfway (geometrically) between two well separated rates at step 15
+    vals = np.sort(np.array([r[14] for r in rates]))
+    gaps = vals[1:] / vals[:-1]
+    i = int(np.argmax(gaps))
+    tol = float(np.sqrt(vals[i] * vals[i + 1]))
+    expect = []
+    for r in rates:
+        below = np.nonzero(r < tol)[0]
+        expect.append(int(below[0]) + 1 if below.size else -1)
+        assert np.all(np.abs(r / tol - 1.0) > 1e-6)        # no rate sits on the tolerance
+    assert len(set(expect)) > 1                           # the runs stop at different steps
+    b = native.Batch(runs, precision=native.PF_FP64)
+    steps = b.run_to_equilibrium(tol=tol, max_steps=nmax, check_every=7)
+    assert list(steps) == expect, (list(steps), expect)
+    for r, s in enumerate(expect):
+        ref = states[r][(s if s > 0 else nmax) - 1]
+        errs = rel_errors(b.get(r, ALL), ref, skip=("Ez", "uz", "P", "ux", "uy", "psi"))
+        assert all(v <= 1e-11 for v in errs.values()), (r, s, errs)
     b.close()
 
 
