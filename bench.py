@@ -161,9 +161,9 @@ def transform_kernel(code, fused_y):
     return name + (" + k_fdm_y" if fused_y and code not in (0, 1, 6, 7) else "")
 
 
-# DRAM traffic per launch of a transform kernel on droplet3d, from one ncu capture of an unchanged
-# kernel (profiles/k_gemm_cp_droplet3d.md): (precision, variant code, fused y) -> bytes
-TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("mixed", 3, 0): 2.24e6}
+# DRAM traffic per launch of a transform kernel, from one ncu capture of an unchanged kernel
+# (profiles/): (workload, precision, variant code, fused y) -> bytes
+TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("droplet3d", "mixed", 3, 0): 2.24e6}
 
 
 def transform_bytes_per_launch(nx, ny, nz, prec):

@@ -23,17 +23,20 @@ def test_transform_kernel_labels_and_traffic_table():
     assert bench.transform_kernel(0, 1) == "k_gemm_tc"
     assert bench.transform_kernel(6, 1) == "k_fdm_cluster<4>"
     # only captured (precision, variant, fused y) triples carry a DRAM traffic figure
-    assert set(bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH) == {("mixed", 3, 0)}
+    assert set(bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH) == {("droplet3d", "mixed", 3, 0)}
     assert bench.transform_bytes_per_launch(128, 65, 64, 1) == pytest.approx(4 * (2 * 128 * 65 * 64 + 128 ** 2))
 
 
 @pytest.mark.parametrize("name", sorted(bench.WORKLOADS))
 def test_every_bench_workload_builds(name):
-    wl = bench.make_workload(name)
-    assert wl.mesh.order >= 2 and wl.scheme.dt > 0
-    x = np.linspace(0.0, 1.0, 7)
-    phi = wl.phi0(x, 0.1 + 0 * x, 0.5 + 0 * x)
-    assert np.all(np.abs(phi) <= 1.0)
+    wls = bench.make_workload(name)
+    for wl in (wls if isinstance(wls, list) else [wls]):
+        assert wl.mesh.order >= 2 and wl.scheme.dt > 0
+        x = np.linspace(0.0, 1.0, 7)
+        phi = wl.phi0(x, 0.1 + 0 * x, 0.5 + 0 * x)
+        assert np.all(np.abs(phi) <= 1.0)
+    if name == "ensemble2d":
+        assert len(wls) == 256 and len({(w.mesh.ex, w.mesh.order) for w in wls}) > 20
 
 
 def test_electrode_array_normalisation():
