@@ -2084,6 +2084,9 @@ void batch_step_once(pf_batch *b) {
             graph_counts(b, c) = before;
         }
         PF_CU(cudaGraphLaunch(b->graph[c], b->st));
+        // later work on the group streams (reads, eager steps) comes after the replayed step
+        PF_CU(cudaEventRecord(b->fork, b->st));
+        for (auto &g : b->groups) PF_CU(cudaStreamWaitEvent(g->gst, b->fork, 0));
         for (size_t i = 0; i < b->groups.size(); ++i) {
             auto &g = *b->groups[i];
             for (int k = 0; k < PF_KC_COUNT; ++k) g.prof.launches[k] += graph_counts(b, c)[i][k];

@@ -10,9 +10,11 @@
 // Persistent, warp-specialised kernel; one CTA per SM walks tiles of 128 rows x BN columns:
 //   warp 8      TMA producer: per 32-wide K chunk, A (128 x 32) and both halves of Bt (BN x 32)
 //               into a ring of shared-memory stages (128-byte swizzle, the layout the MMA reads)
-//   warps 0-7   split each landed A chunk into hi (in place) and lo (a second buffer); drain the
-//               TMEM accumulators into FP32 registers and run the epilogue
+//   warps 10-11 split each landed A chunk into hi (in place) and lo (a second buffer)
 //   warp 9      one thread issues tcgen05.mma (M = 128, N = BN, K = 8) and commits to mbarriers
+//   warps 0-7   drain the TMEM accumulators into FP32 registers (all of a thread's columns loaded
+//               before one wait) and run the epilogue; setmaxnreg moves registers from warps 8-11
+//               (producer, MMA, split) to them
 // The tensor core's FP32 accumulation is not rounded to nearest, and the eigenvector sums cancel
 // heavily, so a chain of MMAs in one accumulator loses digits (chunks of 32 in one region: phi of
 // the 2D droplet drifted 4x further from the oracle in 50 steps than with one region per slice).
@@ -32,8 +34,12 @@ namespace pf {
 
 constexpr int TC_BM = 128;                          // rows per tile = TMEM lanes
 constexpr int TC_KC = 32;                           // K per stage: one 128-byte row of FP32
-constexpr int TC_EPI_WARPS = 8;                     // two warpgroups, one per column half
-constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
+constexpr int TC_EPI_WARPS = 8;                     // warpgroups 0-1: one per column half
+constexpr int TC_CONV_WARPS = 2;                    // warps 10-11: the A split
+constexpr int TC_THREADS = 12 * 32;                 // warpgroup 2: producer, MMA, converters
+// register split (setmaxnreg): the launch holds 384 x 168 = 64512 registers; warpgroup 2 gives
+// back down to 72 a thread and the epilogue warpgroups take 216: 256 x 216 + 128 x 72 = 64512
+constexpr int TC_REG_EPI = 216, TC_REG_AUX = 72;
 constexpr int TC_MAXH = 64;                         // accumulator columns per thread: BN <= 128
 constexpr int TC_MAXR = 8;                          // TMEM regions in the ring at most
 constexpr int TC_ERR_TIMEOUT = 1;                   // error word: a bounded wait gave up
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(b_full + 8 * s, 1);
-            mbar_init(b_conv + 8 * s, TC_EPI_WARPS);
+            mbar_init(b_conv + 8 * s, TC_CONV_WARPS);
             mbar_init(b_empty + 8 * s, 1);
         }
         for (int r = 0; r < TC_MAXR; ++r) {
@@ -218,6 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         *abort_flag = 1;
     };
 
+    if (warp >= TC_EPI_WARPS) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TC_REG_AUX));
     if (warp == TC_EPI_WARPS) {
         // ---- TMA producer -------------------------------------------------------------------
         if (lane == 0) {
@@ -289,42 +296,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_wait(b_stall, 0u, nullptr, g.wait_ns);
         }
         __syncwarp();
-    } else {
-        // ---- split A, drain the accumulators, epilogue (warps 0-7) ----------------------------------
+    } else if (warp < TC_EPI_WARPS) {
+        // ---- drain the accumulators, epilogue (warps 0-7) ----------------------------------------
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TC_REG_EPI));
         const int quarter = warp & 3, half = warp >> 2;
-        const int et = tid;   // 0..255
         float acc[TC_MAXH];
 #pragma unroll
         for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
-        int grp = 0, s = 0, c = 0, t = blockIdx.x;   // c, t: chunk and tile of q - 1
-        uint32_t ph = 0;
+        int grp = 0, c = 0, t = blockIdx.x;   // c, t: chunk and tile of q - 1
         bool ok = true;
-        for (int q = 0; q <= Q && ok; ++q) {
-            // split chunk q: hi in place, lo into the second A buffer (16 floats per thread)
-            if (q < Q) {
-                if (!mbar_wait(b_full + 8 * s, ph, abort_flag, g.wait_ns)) {
-                    ok = false;
-                    break;
-                }
-                unsigned char *sa = base + (size_t)s * STAGE;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t off = (uint32_t)(16 * (et + 256 * i));
-                    const float4 x = *(const float4 *)(sa + off);
-                    float4 h, l;
-                    h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
-                    h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
-                    h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
-                    h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
-                    *(float4 *)(sa + off) = h;
-                    *(float4 *)(sa + ABYTES + off) = l;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(b_conv + 8 * s);
-                if (++s == S) { s = 0; ph ^= 1u; }
-            }
-            if (q == 0) continue;
+        for (int q = 1; q <= Q && ok; ++q) {
             // the groups of chunk q - 1, in K order, into the registers
             const int cd = c, td = t;
             if (++c == nchunk) { c = 0; t += gridDim.x; }
@@ -337,18 +318,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * BN + half * hbn);
+                {   // every column of the group first, then one wait
+                    float v[TC_MAXH];
 #pragma unroll
-                for (int j0 = 0; j0 < TC_MAXH; j0 += 16) {
-                    if (j0 < hbn) {
-                        float v[16];
+                    for (int j0 = 0; j0 < TC_MAXH; j0 += 8)
+                        if (j0 < hbn) tmem_ld8(ta + (uint32_t)j0, v + j0);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int u = 0; u < 2; ++u)
-                            if (j0 + 8 * u < hbn) tmem_ld8(ta + (uint32_t)(j0 + 8 * u), v + 8 * u);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (j0 + j < hbn && j0 + j < TC_MAXH) acc[j0 + j] += v[j];
-                    }
+                    for (int j = 0; j < TC_MAXH; ++j)
+                        if (j < hbn) acc[j] += v[j];
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -414,6 +392,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
         }
         if (!ok) fail();
+    } else {
+        // ---- split A into TF32 head (in place) and tail (warps 10-11: 64 floats a thread) -----
+        const int ct = tid - (TC_EPI_WARPS + 2) * 32;   // 0..63
+        int s = 0;
+        uint32_t ph = 0;
+        for (int q = 0; q < Q; ++q) {
+            if (!mbar_wait(b_full + 8 * s, ph, abort_flag, g.wait_ns)) {
+                fail();
+                break;
+            }
+            unsigned char *sa = base + (size_t)s * STAGE;
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t off = (uint32_t)(16 * (ct + 64 * i));
+                const float4 x = *(const float4 *)(sa + off);
+                float4 h, l;
+                h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+                h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+                h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+                h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+                *(float4 *)(sa + off) = h;
+                *(float4 *)(sa + ABYTES + off) = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_conv + 8 * s);
+            if (++s == S) { s = 0; ph ^= 1u; }
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
