@@ -375,6 +375,12 @@ int pf_no_get_params(pf_no *h, double *host, size_t n);
 int pf_no_set_params(pf_no *h, const double *host, size_t n);
 /* Phase field at the nodes (B x nq, host) for B feature rows (B x dims[0], host). */
 int pf_no_predict(pf_no *h, int B, const double *feat, double *phi_nodes);
+/* As pf_no_predict, then each sample's field is shifted by a constant so that its phase mass
+ * sum_ij wx[j] wy[i] phi_ij equals mass[b] (FP64 sums on the device): the equilibrium system of
+ * Sec. 2.4 conserves int phi, so a warm start carries the run's own mass.  wx[nqx], wy[nqy] are
+ * the quadrature weights of the node grid (the assembled 1D GLL masses), mass[B] the targets. */
+int pf_no_predict_mass(pf_no *h, int B, const double *feat, const double *mass, const double *wx,
+                       const double *wy, double *phi_nodes);
 /* Mean squared error against target node fields (B x nq) and the gradient of every
  * parameter (grad nullable; layout of pf_no_get_params). */
 int pf_no_loss_grad(pf_no *h, int B, const double *feat, const double *target, double *loss, double *grad);

@@ -230,7 +230,10 @@ struct Engine {
     };
     std::vector<TcB> tcb;
     bool use_tc = false;
-    int tc_group = 1;                 // 8-wide K slices per TMEM accumulation group (1, 2 or 4)
+#ifndef PF_TC_SLICES_PER_GROUP
+#define PF_TC_SLICES_PER_GROUP 1
+#endif
+    int tc_group = PF_TC_SLICES_PER_GROUP;   // 8-wide K slices per TMEM accumulation group (1, 2 or 4)
     int tc_stall = 0;                 // test hook: the next tensor-core launch reports a time-out
     unsigned long long tc_wait_ns = 1000000000ull;   // bound of every wait (1 s)
     unsigned long long tc_wait_ns_next = 0;          // the test hook's bound

@@ -160,9 +160,40 @@ __global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict
 
 }  // namespace
 
+// Mass projection of predicted node fields (one block per sample): phi += (target - sum w phi) /
+// sum w with the tensor-product quadrature weights w_ij = wx[j] wy[i]; FP64 sums.  A constant shift
+// is the L2-closest field with the prescribed phase mass int phi.
+__global__ void k_mass_shift(float *__restrict__ pn, int nqx, int nqy, const double *__restrict__ wx,
+                             const double *__restrict__ wy, const double *__restrict__ target) {
+    const int b = blockIdx.x, nq = nqx * nqy;
+    float *p = pn + (size_t)b * nq;
+    __shared__ double ss[256], sw[256];
+    double s = 0.0, w = 0.0;
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+        const double wi = wx[i % nqx] * wy[i / nqx];
+        s += wi * (double)p[i];
+        w += wi;
+    }
+    ss[threadIdx.x] = s;
+    sw[threadIdx.x] = w;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            ss[threadIdx.x] += ss[threadIdx.x + k];
+            sw[threadIdx.x] += sw[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    const double c = (target[b] - ss[0]) / sw[0];
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) p[i] = (float)((double)p[i] + c);
+}
+
 struct pf_no {
     std::vector<int> dims;                 // layer widths, dims[0] = 3
     int ng = 0, nq = 0, maxB = 0;
+    int nqx = 0, nqy = 0;                  // node grid of the predictions ([y][x], x fastest)
+    double *mw = nullptr;                  // mass projection: wx[nqx], wy[nqy], target[B]
+    int mw_B = 0;
     cudaStream_t st = nullptr;
     // parameters: per layer W (dims[l] x dims[l+1]) then b (dims[l+1]), one flat FP32 master array
     std::vector<long long> woff, boff;
@@ -298,6 +329,8 @@ extern "C" int pf_no_create(int nlayer, const int *dims, const double *feat_mean
         h->st = (cudaStream_t)cuda_stream;
         h->ng = gnx * gny;
         h->nq = nqx * nqy;
+        h->nqx = nqx;
+        h->nqy = nqy;
         long long off = 0;
         for (int l = 0; l + 1 < nlayer; ++l) {
             h->woff.push_back(off);
@@ -425,6 +458,33 @@ extern "C" int pf_no_predict(pf_no *h, int B, const double *feat, double *phi_no
         ensure_batch(h, B);
         upload_features(h, B, feat);
         forward(h, B);
+        std::vector<float> p((size_t)B * h->nq);
+        NO_CU(cudaMemcpyAsync(p.data(), h->pn, p.size() * 4, cudaMemcpyDeviceToHost, h->st));
+        NO_CU(cudaStreamSynchronize(h->st));
+        for (size_t i = 0; i < p.size(); ++i) phi_nodes[i] = p[i];
+    } catch (const NoErr &e) {
+        return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_no_predict_mass(pf_no *h, int B, const double *feat, const double *mass, const double *wx,
+                                  const double *wy, double *phi_nodes) {
+    if (!h || B < 1 || !feat || !mass || !wx || !wy || !phi_nodes)
+        return no_fail(PF_EINVAL, "pf_no_predict_mass: bad arguments");
+    try {
+        ensure_batch(h, B);
+        upload_features(h, B, feat);
+        forward(h, B);
+        if (B > h->mw_B) {
+            h->mw = h->mk<double>((size_t)h->nqx + h->nqy + B);
+            h->mw_B = B;
+        }
+        NO_CU(cudaMemcpyAsync(h->mw, wx, h->nqx * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        NO_CU(cudaMemcpyAsync(h->mw + h->nqx, wy, h->nqy * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        NO_CU(cudaMemcpyAsync(h->mw + h->nqx + h->nqy, mass, B * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        k_mass_shift<<<B, 256, 0, h->st>>>(h->pn, h->nqx, h->nqy, h->mw, h->mw + h->nqx, h->mw + h->nqx + h->nqy);
+        NO_CU(cudaGetLastError());
         std::vector<float> p((size_t)B * h->nq);
         NO_CU(cudaMemcpyAsync(p.data(), h->pn, p.size() * 4, cudaMemcpyDeviceToHost, h->st));
         NO_CU(cudaStreamSynchronize(h->st));

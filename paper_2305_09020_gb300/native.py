@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
     L.pf_no_get_params.argtypes = [c_void_p, dp, c_size_t]
     L.pf_no_set_params.argtypes = [c_void_p, dp, c_size_t]
     L.pf_no_predict.argtypes = [c_void_p, c_int, dp, dp]
+    L.pf_no_predict_mass.argtypes = [c_void_p, c_int, dp, dp, dp, dp, dp]
     L.pf_no_loss_grad.argtypes = [c_void_p, c_int, dp, dp, dp, dp]
     L.pf_no_train.argtypes = [c_void_p, c_int, dp, dp, c_int, c_int, c_double, ctypes.c_uint64, dp]
     L.pf_no_destroy.argtypes = [c_void_p]
@@ -472,6 +473,17 @@ class NeuralOperator:
         feat = _f64(feat).reshape(-1, self.dims[0])
         out = np.zeros((feat.shape[0], self.nq))
         _check(load().pf_no_predict(self._h, feat.shape[0], _dp(feat), _dp(out)), None)
+        return out
+
+    def predict_mass(self, feat, mass, wx, wy):
+        """Predictions shifted to the phase masses ``mass`` (quadrature weights wx, wy)."""
+        feat = _f64(feat).reshape(-1, self.dims[0])
+        mass, wx, wy = _f64(mass).ravel(), _f64(wx).ravel(), _f64(wy).ravel()
+        if mass.size != feat.shape[0]:
+            raise ValueError("one target mass per feature row")
+        out = np.zeros((feat.shape[0], self.nq))
+        _check(load().pf_no_predict_mass(self._h, feat.shape[0], _dp(feat), _dp(mass), _dp(wx), _dp(wy),
+                                         _dp(out)), None)
         return out
 
     def loss_grad(self, feat, target):
