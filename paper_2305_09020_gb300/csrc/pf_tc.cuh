@@ -118,24 +118,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of `parity` to complete.  Gives up (false) after limit_ns of waiting, or at
-// once when another thread of the CTA has raised the abort flag (abort may be null).
+// Wait for the phase of `parity` to complete.  Gives up (false) after about limit_ns of waiting
+// (counted in SM clock cycles at up to 2.5 GHz: the cycle counter is cheap to read, unlike the
+// global timer), or at once when another thread of the CTA has raised the abort flag (abort may
+// be null).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort,
                                           unsigned long long limit_ns) {
-    unsigned long long t0 = 0;
+    if (mbar_try(mbar, parity)) return true;
+    const long long t0 = clock64();
+    const long long limit = (long long)(limit_ns * 5ull / 2ull);   // cycles
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(mbar, parity)) return true;
-        if ((it & 31u) == 31u) {
+        if ((it & 15u) == 15u) {
             if (abort && *abort) return false;
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > limit_ns) return false;
+            if (clock64() - t0 > limit) return false;
         }
     }
 }
