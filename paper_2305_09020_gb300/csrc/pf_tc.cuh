@@ -106,14 +106,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
+// One test of the phase; a thread whose phase is not complete sleeps in hardware (up to a
+// microsecond) until it completes instead of spinning: waiting warps leave the issue slots to the
+// warps that work.
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(1000u)
         : "memory");
     return done != 0;
 }
@@ -127,12 +130,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const 
     if (mbar_try(mbar, parity)) return true;
     const long long t0 = clock64();
     const long long limit = (long long)(limit_ns * 5ull / 2ull);   // cycles
-    for (uint32_t it = 0;; ++it) {
+    for (;;) {
         if (mbar_try(mbar, parity)) return true;
-        if ((it & 15u) == 15u) {
-            if (abort && *abort) return false;
-            if (clock64() - t0 > limit) return false;
-        }
+        if (abort && *abort) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
