@@ -774,31 +774,32 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     }
     __syncthreads();
     const long long lplane = (long long)G.ex * G.ey * G.p * G.p;
-    const int total = tp * nz;
-    const int lgtp = 31 - __clz(tp);          // tp is a power of two
-    for (int base = threadIdx.x; base < total; base += 4 * blockDim.x) {
-        T v0[4], v1[4];
+    const int lgtp = 31 - __clz(tp);          // tp is a power of two dividing blockDim.x
+    {
+        // this thread's pencil column is fixed (blockDim.x is a multiple of tp): its DSSUM sources
+        // live in registers, and it walks the planes z0, z0 + zs, ... eight gathers at a time
+        const int ql = threadIdx.x & (tp - 1), qg = q0 + ql, z0 = threadIdx.x >> lgtp, zs = blockDim.x >> lgtp;
+        int sr[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {   // four independent gathers in flight
-            const int idx = base + u * blockDim.x;
-            v0[u] = 0;
-            v1[u] = 0;
-            if (idx < total) {
-                const int z = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
-                if (qg < G.n2) {
+        for (int c = 0; c < 4; ++c) sr[c] = ssrc[ql * 4 + c];
+        const bool live = qg < G.n2;
+        for (int zb = z0; zb < nz; zb += 8 * zs) {
+            T v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {   // eight independent gathers in flight
+                const int z = zb + u * zs;
+                v0[u] = 0;
+                v1[u] = 0;
+                if (live && z < nz) {
                     const long long gi = (long long)z * G.n2 + qg;
-                    const int *s = ssrc + ql * 4;
-                    v0[u] = a.x0_local ? gather4(a.X0, z * lplane, s) : a.X0[gi];
-                    if (a.X1) v1[u] = a.x1_local ? gather4(a.X1, z * lplane, s) : a.X1[gi];
+                    v0[u] = a.x0_local ? gather4(a.X0, z * lplane, sr) : a.X0[gi];
+                    if (a.X1) v1[u] = a.x1_local ? gather4(a.X1, z * lplane, sr) : a.X1[gi];
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * blockDim.x;
-            if (idx < total) {
-                const int z = idx >> lgtp, ql = idx & (tp - 1);
-                buf[ql * ld + fft_slot(z, bits, pow2)] = {v0[u], v1[u]};
+            for (int u = 0; u < 8; ++u) {
+                const int z = zb + u * zs;
+                if (z < nz) buf[ql * ld + fft_slot(z, bits, pow2)] = {v0[u], v1[u]};
             }
         }
     }
@@ -897,35 +898,52 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     const int q0 = blockIdx.x * tp;
     // load the half spectra: one (k) per thread-iteration, both Re and Im planes
     const int nk = nz / 2 + 1;
-    const int lgtp = 31 - __clz(tp);          // tp is a power of two
-    for (int idx = threadIdx.x; idx < tp * (nz > 1 ? nk : 1); idx += blockDim.x) {
-        const int k = idx >> lgtp, ql = idx & (tp - 1), qg = q0 + ql;
-        cplx<T> X = {0, 0}, Wk = {0, 0};
-        if (qg < G.n2) {
-            int pre, pim;
-            if (nz == 1 || k == 0) { pre = 0; pim = -1; }
-            else if (k == nz / 2) { pre = 1; pim = -1; }
-            else { pre = 2 * k; pim = 2 * k + 1; }
-            auto ld2 = [&](const T *A) -> cplx<T> {
-                cplx<T> r = {A[(long long)pre * G.n2 + qg], pim >= 0 ? A[(long long)pim * G.n2 + qg] : T(0)};
-                return r;
-            };
-            X = ld2(a.Y);
-            if (k == 0 && a.drow0 >= 0 && qg / G.nx == a.drow0) X.x += a.v0;
-            if (k == 0 && a.drow1 >= 0 && qg / G.nx == a.drow1) X.x += a.v1;
-            if (a.phi_variant) {
-                const cplx<T> ps = ld2(a.psi), q2 = ld2(a.Q2h);
-                const T c = a.alpha + a.S_eta2;
-                Wk = {ps.x - c * X.x - q2.x, ps.y - c * X.y - q2.y};
+    const int lgtp = 31 - __clz(tp);          // tp is a power of two dividing blockDim.x
+    {
+        // fixed pencil column per thread; modes k0, k0 + ks, ... four at a time, loads first
+        const int ql = threadIdx.x & (tp - 1), qg = q0 + ql, k0 = threadIdx.x >> lgtp, ks = blockDim.x >> lgtp;
+        const int nkk = nz > 1 ? nk : 1;
+        const bool live = qg < G.n2;
+        const int row = live ? qg / G.nx : -1;
+        for (int kb = k0; kb < nkk; kb += 4 * ks) {
+            cplx<T> X[4], PS[4], Q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = kb + u * ks;
+                X[u] = PS[u] = Q[u] = cplx<T>{0, 0};
+                if (live && k < nkk) {
+                    int pre, pim;
+                    if (nz == 1 || k == 0) { pre = 0; pim = -1; }
+                    else if (k == nz / 2) { pre = 1; pim = -1; }
+                    else { pre = 2 * k; pim = 2 * k + 1; }
+                    const long long ore = (long long)pre * G.n2 + qg, oim = (long long)pim * G.n2 + qg;
+                    X[u] = {a.Y[ore], pim >= 0 ? a.Y[oim] : T(0)};
+                    if (a.phi_variant) {
+                        PS[u] = {a.psi[ore], pim >= 0 ? a.psi[oim] : T(0)};
+                        Q[u] = {a.Q2h[ore], pim >= 0 ? a.Q2h[oim] : T(0)};
+                    }
+                }
             }
-        }
-        const T beta = a.two_pi_over_lz * T(k);
-        if (nz == 1) {
-            buf[ql * ld] = X;
-            if (a.phi_variant) buf[(tp + ql) * ld] = Wk;
-        } else {
-            put_pair(buf + ql * ld, nz, bits, pow2, k, X, beta);
-            if (a.phi_variant) put_pair(buf + (tp + ql) * ld, nz, bits, pow2, k, Wk, beta);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = kb + u * ks;
+                if (k >= nkk) continue;
+                cplx<T> Xk = X[u], Wk = {0, 0};
+                if (k == 0 && a.drow0 >= 0 && row == a.drow0) Xk.x += a.v0;
+                if (k == 0 && a.drow1 >= 0 && row == a.drow1) Xk.x += a.v1;
+                if (a.phi_variant) {
+                    const T c = a.alpha + a.S_eta2;
+                    Wk = {PS[u].x - c * Xk.x - Q[u].x, PS[u].y - c * Xk.y - Q[u].y};
+                }
+                const T beta = a.two_pi_over_lz * T(k);
+                if (nz == 1) {
+                    buf[ql * ld] = Xk;
+                    if (a.phi_variant) buf[(tp + ql) * ld] = Wk;
+                } else {
+                    put_pair(buf + ql * ld, nz, bits, pow2, k, Xk, beta);
+                    if (a.phi_variant) put_pair(buf + (tp + ql) * ld, nz, bits, pow2, k, Wk, beta);
+                }
+            }
         }
     }
     __syncthreads();
