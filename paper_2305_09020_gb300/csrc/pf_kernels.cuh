@@ -113,6 +113,14 @@ struct ElemIdx {
     long long l;    // element-local slot (with plane offset)
 };
 
+// Element-local arrays (weak-form contributions before direct stiffness summation) are stored
+// row-interleaved, [z][e_y][b][e_x][a]: the slots of one global node row lie next to each other
+// (with the duplicated element-boundary slots adjacent), so the summation's gathers coalesce.
+template <typename T>
+__device__ __forceinline__ long long eloc(const Geo<T> &G, long long z, int ey, int ex, int b, int a) {
+    return z * ((long long)G.ex * G.ey * G.p * G.p) + ((long long)(ey * G.p + b) * G.ex + ex) * G.p + a;
+}
+
 // blockIdx.x: group of G.epb elements of plane blockIdx.y; thread = (local element, node)
 template <typename T>
 __device__ __forceinline__ ElemIdx elem_index(const Geo<T> &G) {
@@ -131,7 +139,7 @@ __device__ __forceinline__ ElemIdx elem_index(const Geo<T> &G) {
     int xi = e.ex * G.K + e.a;
     if (xi >= G.nx) xi -= G.nx;
     e.g = (long long)e.z * G.n2 + (long long)(e.ey * G.K + e.b) * G.nx + xi;
-    e.l = ((long long)e.z * G.ex * G.ey + elc) * pp + e.t;
+    e.l = eloc(G, e.z, e.ey, e.ex, e.b, e.a);
     return e;
 }
 
@@ -531,11 +539,9 @@ __device__ __forceinline__ T dssum(const Geo<T> &G, const T *__restrict__ Lv, in
     } else {
         exs[nx_] = j / K; as[nx_++] = j % K;
     }
-    const long long base = (long long)z * G.ex * G.ey;
     T s = 0;
     for (int cy = 0; cy < ny_; ++cy)
-        for (int cx = 0; cx < nx_; ++cx)
-            s += Lv[(base + (long long)eys[cy] * G.ex + exs[cx]) * (p * p) + bs[cy] * p + as[cx]];
+        for (int cx = 0; cx < nx_; ++cx) s += Lv[eloc(G, z, eys[cy], exs[cx], bs[cy], as[cx])];
     return s;
 }
 
@@ -735,7 +741,7 @@ __device__ __forceinline__ void dss_sources(const Geo<T> &G, int q, int src[4]) 
     }
     int c = 0;
     for (int cy = 0; cy < ny_; ++cy)
-        for (int cx = 0; cx < nx_; ++cx) src[c++] = (eys[cy] * G.ex + exs[cx]) * (p * p) + bs[cy] * p + as[cx];
+        for (int cx = 0; cx < nx_; ++cx) src[c++] = (int)eloc(G, 0, eys[cy], exs[cx], bs[cy], as[cx]);
     for (; c < 4; ++c) src[c] = -1;
 }
 
