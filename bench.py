@@ -190,88 +190,53 @@ def fdm_flops_per_step(nx, ny, nz, d3, equilibrium=False, patches=False):
 
 
 def warmstart_arm(args):
-    """Learned warm start: steps and wall time to equilibrium, warm vs cold (opt-in; minutes)."""
+    """Learned warm start of the equilibrium system (Sec. 2.4, FP64 pseudo-time march): steps and
+    wall time to the criterion, warm vs cold, and the error of both against a judge (the cold start
+    run to a tolerance ten times tighter).  Opt-in; minutes of GPU time."""
     import numpy as np
     import torch
     import workloads
     from paper_2305_09020_gb300 import native, warmstart
     stream = torch.cuda.Stream()
-    tol, cap, every = args.ws_tol, args.ws_cap, 200
-    train = workloads.warmstart2d(args.ws_train, seed=1)
-    test = workloads.warmstart2d(args.ws_test, seed=10001)
+    tol, cap, every = args.ws_tol, args.ws_cap, 500
+    train = warmstart.equilibrium_runs(workloads.warmstart2d(args.ws_train, seed=1))
+    test = warmstart.equilibrium_runs(workloads.warmstart2d(args.ws_test, seed=10001))
     t0 = time.perf_counter()
-    f_tr, y_tr, st_tr = warmstart.generate(train, tol, cap, every, stream=stream.cuda_stream)
+    f_tr, y_tr, st_tr = warmstart.generate(train, tol, cap, every, precision=native.PF_FP64, stream=stream.cuda_stream)
     t_gen = time.perf_counter() - t0
     no = warmstart.make_operator(f_tr, train[0].mesh, seed=0, stream=stream.cuda_stream)
     t0 = time.perf_counter()
     losses = no.train(f_tr, y_tr, batch=64, epochs=args.ws_epochs, lr=1e-3, seed=0)
     t_train = time.perf_counter() - t0
-    res = warmstart.evaluate(no, test, tol, cap, every, stream=stream.cuda_stream)
+    res = warmstart.evaluate(no, test, tol, cap, every, precision=native.PF_FP64, stream=stream.cuda_stream,
+                             judge_tol=tol / 10, judge_steps=4 * cap)
     no.close()
+    ec, ew = np.array(res["cold"]["err"]), np.array(res["warm"]["err"])
+    same = ew <= 3.0 * ec + 1e-4
+    sc, sw = np.array(res["cold"]["steps"]), np.array(res["warm"]["steps"])
+    for k in ("cold", "warm"):
+        res[k].pop("steps")
+        res[k].pop("err")
     line = {"metric": "time-to-equilibrium warm vs cold", "unit": "s", "higher_is_better": False,
             "value": res["warm"]["run_s"], "cold_value": res["cold"]["run_s"],
-            "criterion": f"max|u| < {tol:g} checked every {every} steps, cap {cap} steps",
+            "criterion": f"max|phi^(n+1) - phi^n| / dt < {tol:g} (equilibrium system, pseudo-time), exit on the "
+                         f"device per run, cap {cap} steps; judge: the cold start to {tol / 10:g}",
             "config": {"workload": "warm-start ensemble: 16x8 elements order 8, V~U(0,3), eps ratio logU(2,20), "
-                                   "drop radius U(0.15,0.35) on the wall, eta 0.02, dt 1e-4, mixed precision",
+                                   "drop radius U(0.15,0.35) on the wall, eta 0.02; equilibrium system, dt 1e-3, "
+                                   "mobility 3e-3, FP64",
                        "train_runs": len(train), "test_runs": len(test), "seeds": "train 1, test 10001",
-                       "network": "3-128-384-8192 tanh MLP, 128x64 grid, bilinear to GLL nodes, BF16 weights"},
-            "cold": res["cold"], "warm": res["warm"], "final_phi_rel_diff": res["final_phi_rel_diff_warm_vs_cold"],
+                       "network": "3-128-384-8192 tanh MLP, 128x64 grid, bilinear to GLL nodes, BF16 weights; "
+                                  "prediction shifted on the device to each run's phase mass"},
+            "cold": res["cold"], "warm": res["warm"], "judge": res["judge"],
+            "warm_runs_at_the_judges_equilibrium": float(same.mean()),
+            "steps_median_where_both_agree": {"cold": float(np.median(sc[same])) if same.any() else None,
+                                              "warm": float(np.median(sw[same])) if same.any() else None},
+            "final_phi_rel_diff": res["final_phi_rel_diff_warm_vs_cold"],
             "train": {"generation_s": t_gen, "training_s": t_train, "epochs": args.ws_epochs,
                       "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-                      "train_runs_reaching_tol": int((st_tr >= 0).sum())}}
+                      "train_runs_reaching_tol": int((st_tr > 0).sum())}}
     print(json.dumps(line))
     return 0
-
-
-# pinned FP64 transform variant per workload (what the autotuner picks on the GB300): cp.async 32x32
-# tiles with the fused y pair
-FP64_VARIANT = (4, 1)
-# timed oracle steps of the CPU baseline per workload (about 10-30 s of host work)
-ORACLE_STEPS = {"layers3d": 10, "droplet3d": 10, "electrode_array3d": 5, "patches2d": 10}
-
-
-def fp64_leg(args, wl, dof, prec, gemm_choice, fused_y, fft_tile, stream, flush, barrier):
-    """The FP64 path on the same workload: its rate (graph replays, L2 flushed between steps), and
-    the per-field relative L2 difference of the mixed path (the timed variant pinned) after
-    args.err_steps steps from the same initial state.  The FP64 path is itself held to 1e-11 of
-    the FP64 oracle by the parity tests."""
-    import numpy as np
-    import torch
-    from paper_2305_09020_gb300 import native
-    ALL_FIELDS = (native.PF_FIELD_V | native.PF_FIELD_E | native.PF_FIELD_PHI | native.PF_FIELD_PSI |
-                  native.PF_FIELD_P | native.PF_FIELD_U)
-    h64 = native.from_workload(wl, precision=native.PF_FP64, stream=stream.cuda_stream)
-    h64.set_variant(*FP64_VARIANT)
-    hm = native.from_workload(wl, precision=prec, stream=stream.cuda_stream)
-    hm.set_variant(gemm_choice, fuse_y=bool(fused_y), tile=fft_tile)
-    n = max(1, args.err_steps)
-    h64.step(n)
-    hm.step(n)
-    f64, fm = h64.get(ALL_FIELDS), hm.get(ALL_FIELDS)
-    hm.close()
-    err = {}
-    for k in f64:
-        nrm = float(np.linalg.norm(f64[k]))
-        if nrm > 0:
-            err[k] = float(np.linalg.norm(fm[k] - f64[k]) / nrm)
-    k64 = 3
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
-    barrier()
-    for k in range(k64):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        ev[k][0].record(stream)
-        h64.step(1)
-        ev[k][1].record(stream)
-    barrier()
-    ms64 = sum(a.elapsed_time(b) for a, b in ev) / k64
-    h64.close()
-    return {"value": dof / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
-            "variant": transform_kernel(*FP64_VARIANT) + " (FP64, pinned)",
-            "err_steps": n,
-            "mixed_rel_l2_vs_fp64": err,
-            "note": "relative L2 per field of the mixed path against the FP64 GPU path after err_steps steps "
-                    "from the same initial state; the FP64 path matches the FP64 oracle to 1e-11 (tests)"}
 
 
 def ensemble_arm(args):
@@ -360,7 +325,7 @@ def main():
     ap.add_argument("--warmstart", action="store_true", help="learned warm start study instead (minutes)")
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
-    ap.add_argument("--ws-tol", type=float, default=1e-2)
+    ap.add_argument("--ws-tol", type=float, default=1e-3)
     ap.add_argument("--ws-cap", type=int, default=20000)
     ap.add_argument("--ws-epochs", type=int, default=200)
     args = ap.parse_args()

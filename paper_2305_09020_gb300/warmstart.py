@@ -3,9 +3,12 @@
 Orchestration only: every time step runs in the ensemble engine (pf_batch_*), every network
 forward/backward/update in the library's kernels (pf_no_*); this module moves arrays.
 
-* ``generate``   runs batches of independent 2D runs on one fixed mesh until every run has
-  max|u| < tol or the step cap, and returns the run features (V, permittivity ratio, drop
-  area), the phase field at the end (the equilibrium target) and the steps each run needed.
+* ``equilibrium_runs`` switches runs to the pseudo-time march of the equilibrium system (Sec. 2.4).
+* ``generate``   runs batches of independent 2D runs on one fixed mesh until every run meets the
+  criterion (max|u|, or for the equilibrium system the pseudo-time rate, below tol; each run
+  exits on the device at its own step) or the step cap, and returns the run features (V,
+  permittivity ratio, drop area), the phase field at the exit (the equilibrium target) and the
+  steps each run needed.
 * ``make_operator`` / ``train``  the network of ``native.NeuralOperator``: 3 -> 128 -> 384 ->
   128x64 grid (tanh), bilinear to the GLL nodes, BF16 weights.
 * ``evaluate``  runs held-out cases from the usual initial profile (cold) and from the network's
@@ -26,6 +29,18 @@ from . import native
 GRID = (128, 64)
 BOX = (0.0, 2.0, 0.0, 1.0)
 DIMS = [3, 128, 384, GRID[0] * GRID[1]]
+
+
+def equilibrium_runs(runs: List[workloads.Workload], dt: float = 1e-3, gamma1: float = 3e-3):
+    """The runs marched with the simpler equilibrium system of Sec. 2.4 (eq. 16 with eq. 15c, 15d,
+    u = 0) in pseudo-time.  Its steady states do not depend on the mobility or the time step, so
+    both are taken larger than in the full model (faster relaxation; at mobility 1e-2 some runs
+    of this family diverge)."""
+    for w in runs:
+        w.scheme.equilibrium = True
+        w.scheme.dt = dt
+        w.fluid.gamma1 = gamma1
+    return runs
 
 
 def _chunks(seq, n):

@@ -67,3 +67,37 @@ def test_warm_start_prediction_beats_cold_profile():
     e_cold = np.linalg.norm(cold - y_te, axis=1)
     assert np.median(e_warm) < np.median(e_cold), (np.median(e_warm), np.median(e_cold))
     no.close()
+
+
+def test_warm_start_saves_steps_to_the_equilibrium():
+    """The equilibrium system (Sec. 2.4) on a coarse mesh, FP64: trained on the equilibria of 256
+    runs, the network's fields (shifted on the device to each run's phase mass) start 24 held-out
+    runs that reach the pseudo-time criterion in fewer steps (median) than the same runs started
+    cold; the judge is the cold start run to a tolerance ten times tighter.  Most warm runs end at
+    the judge's equilibrium as closely as the cold runs do; some settle in another steady state,
+    which the judge exposes (the cold start stays the fallback)."""
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+
+    def runs(n, seed):
+        out = workloads.warmstart2d(n, seed)
+        for w in out:
+            w.mesh = workloads.Mesh(xb=np.linspace(0, 2, 9), yb=np.linspace(0, 1, 5), order=6)
+        return warmstart.equilibrium_runs(out)
+
+    tol, cap = 1e-3, 20000
+    train, test = runs(256, 101), runs(24, 202)
+    f_tr, y_tr, st_tr = warmstart.generate(train, tol=tol, max_steps=cap, check_every=500,
+                                           precision=native.PF_FP64, stream=s.cuda_stream)
+    assert (st_tr > 0).sum() > 200                        # the training targets are equilibria
+    no = warmstart.make_operator(f_tr, train[0].mesh, seed=0, stream=s.cuda_stream)
+    no.train(f_tr, y_tr, batch=32, epochs=600, lr=1e-3, seed=0)
+    res = warmstart.evaluate(no, test, tol, cap, check_every=500, precision=native.PF_FP64,
+                             stream=s.cuda_stream, judge_tol=tol / 10, judge_steps=4 * cap)
+    no.close()
+    cold, warm = res["cold"], res["warm"]
+    assert warm["steps_median"] < 0.95 * cold["steps_median"], (warm["steps_median"], cold["steps_median"])
+    ec, ew = np.array(cold["err"]), np.array(warm["err"])
+    assert np.all(ec < 1e-3)                              # the criterion puts cold runs at the judge
+    same = ew <= 3.0 * ec + 1e-4
+    assert same.mean() >= 0.5, (ew, ec)
