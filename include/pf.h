@@ -245,6 +245,11 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
  *   PF_GEMM_TC       3xTF32 tcgen05 tensor-core transforms: persistent warp-specialised kernel,
  *                    TMA-staged operands, FP32 sums of per-K-chunk TMEM accumulators (PF_MIXED
  *                    only; n_x a multiple of 4, for the 16-byte row pitch TMA needs)
+ *   PF_GEMM_TC_HYBRID
+ *                    the psi and phi solves (the Cahn-Hilliard pair of eq. 44, whose rounding drives the
+ *                    phase field's error) on the cp.async 64x64 CUDA-core transforms; the potential,
+ *                    pressure and velocity solves on the tensor cores with four 8-wide K slices per
+ *                    TMEM accumulation group (1.6x faster, less accurate; PF_MIXED only)
  *   PF_GEMM_PLANE    the whole solve of a mode plane in one thread block, plane and eigenbases
  *                    in shared memory (FP32 precisions; n_x <= 128, n_y <= 128)
  *   PF_GEMM_SIMT32 / PF_GEMM_SIMT64 / PF_GEMM_SIMT32X64
@@ -268,13 +273,14 @@ int pf_profile_read(pf_handle *h, double *ms, long long *launches);
 #define PF_GEMM_PIPE32X64 5
 #define PF_GEMM_CLUSTER4 6
 #define PF_GEMM_CLUSTER2 7
+#define PF_GEMM_TC_HYBRID 8
 
 /* Autotuner of a single run: time `steps` steady steps with each transform variant available to
  * the run (PF_GEMM_*), keep the fastest, then (unless a whole-plane variant won) whether the y transforms
  * run fused (one pass, eigenbasis in shared memory), then (3D) the z-transform tile of 4, 8, 16
  * or 32 pencils per block.  Each candidate is timed as the run executes its steady steps: graph
  * replays when the run has its own stream, eager launches on the legacy stream.  The run advances
- * by 15 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile + 100000 * fused_y with
+ * by 16 (steps + 2) steps.  choice (nullable) receives gemm + 1000 * tile + 100000 * fused_y with
  * gemm a PF_GEMM_* code, tile the pencils per z-transform block (0: size heuristic, always 0 in
  * 2D) and fused_y 1 when the y pair runs fused; ms_per_step (nullable) the best time. */
 int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);

@@ -814,14 +814,20 @@ struct Engine {
     }
     // transform variant by its public code (PF_GEMM_*); false when this engine cannot run it
     bool gemm_available(int code) const {
-        return (code == 0 && !tcb.empty()) || (code == 1 && plane_fits()) || code == 32 || code == 64 ||
-               (code >= 2 && code <= 5) || (code == 6 && cluster_fits(4)) || (code == 7 && cluster_fits(2));
+        return ((code == 0 || code == 8) && !tcb.empty()) || (code == 1 && plane_fits()) || code == 32 ||
+               code == 64 || (code >= 2 && code <= 5) || (code == 6 && cluster_fits(4)) ||
+               (code == 7 && cluster_fits(2));
     }
+    // PF_GEMM_TC_HYBRID (8): the psi and phi solves (the natural-BC set) on the cp.async 64x64 SIMT
+    // transforms, the others on the tensor cores with four K slices per accumulation group
+    bool tc_hybrid = false;
     void set_gemm(int code) {
-        use_tc = code == 0;
+        use_tc = code == 0 || code == 8;
+        tc_hybrid = code == 8;
+        tc_group = code == 8 ? 4 : PF_TC_SLICES_PER_GROUP;
         fuse_plane = code == 1;
         cluster = code == 6 ? 4 : code == 7 ? 2 : 0;
-        simt_tile = (code == 32 || code == 64 || (code >= 2 && code <= 5)) ? code : 0;
+        simt_tile = (code == 32 || code == 64 || (code >= 2 && code <= 5)) ? code : code == 8 ? 3 : 0;
     }
     template <int CQ>
     void launch_plane(const T *rhs, T *out, int bcset, const T *sh, long long P, T *c2, const T *face) {
@@ -835,7 +841,7 @@ struct Engine {
     void fdm(const T *rhs, T *out, int bcset, const T *sh, int nplanes, T *minus_m_out = nullptr,
              const T *face = nullptr) {
         const long long P = nplanes;
-        if (use_tc && !tcb.empty()) {
+        if (use_tc && !tcb.empty() && !(tc_hybrid && bcset == PF_BCSET_NN)) {
             fdm_tc(rhs, out, bcset, sh, P, minus_m_out, face);
             return;
         }
@@ -1841,7 +1847,7 @@ void autotune_engine(Engine<T> &E, int steps, int total, cudaEvent_t e0, cudaEve
     };
     // every variant this engine can run (PF_GEMM_* codes)
     std::vector<int> cands;
-    for (int code : {0, 32, 64, 2, 3, 4, 5, 1, 6, 7})
+    for (int code : {0, 8, 32, 64, 2, 3, 4, 5, 1, 6, 7})
         if (E.gemm_available(code)) cands.push_back(code);
     int pick = cands[0];
     double best = INFINITY;
@@ -1880,7 +1886,7 @@ extern "C" int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_
     if (!h || steps < 1) return PF_EINVAL;
     try {
         if (h->nstep < 1) pf_step(h, 1);
-        int total = 15 * (steps + 2);   // at most 10 GEMM variants + the y pair + 4 tiles
+        int total = 16 * (steps + 2);   // at most 11 transform variants + the y pair + 4 tiles
         cudaEvent_t e0, e1;
         PF_CU(cudaEventCreate(&e0));
         PF_CU(cudaEventCreate(&e1));

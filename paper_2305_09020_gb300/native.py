@@ -25,6 +25,7 @@ PF_MODEL_FULL, PF_MODEL_EQUILIBRIUM = 0, 1
 PF_GEMM_TC, PF_GEMM_PLANE, PF_GEMM_SIMT32, PF_GEMM_SIMT64, PF_GEMM_SIMT32X64 = 0, 1, 32, 64, 2
 PF_GEMM_PIPE64, PF_GEMM_PIPE32, PF_GEMM_PIPE32X64 = 3, 4, 5
 PF_GEMM_CLUSTER4, PF_GEMM_CLUSTER2 = 6, 7
+PF_GEMM_TC_HYBRID = 8
 PF_FIELD_V, PF_FIELD_E, PF_FIELD_PHI, PF_FIELD_PSI, PF_FIELD_P, PF_FIELD_U, PF_FIELD_OLD = \
     1, 2, 4, 8, 16, 32, 64
 KERNEL_CLASSES = ["gemm", "fwd", "inv", "potential", "chem", "momentum", "ugradp", "efield", "other"]

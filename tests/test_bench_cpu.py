@@ -22,6 +22,7 @@ def test_transform_kernel_labels_and_traffic_table():
     assert bench.transform_kernel(64, 1) == "k_gemm + k_fdm_y"
     assert bench.transform_kernel(0, 1) == "k_gemm_tc"
     assert bench.transform_kernel(6, 1) == "k_fdm_cluster<4>"
+    assert bench.transform_kernel(8, 1) == "k_gemm_tc + k_gemm_cp"
     # only captured (precision, variant, fused y) triples carry a DRAM traffic figure
     assert set(bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH) == {("droplet3d", "mixed", 3, 0)}
     assert bench.transform_bytes_per_launch(128, 65, 64, 1) == pytest.approx(4 * (2 * 128 * 65 * 64 + 128 ** 2))
@@ -51,3 +52,25 @@ def test_electrode_array_normalisation():
     assert len(pats) == 10 and all(abs(b - a - 1.0 / 12.0) < 1e-15 for a, b, _ in pats)
     assert [v for _, _, v in pats] == [1.0, -1.0] * 5
     assert wl.mesh.nz == 120 and wl.scheme.equilibrium
+
+
+def test_bench_functions_name_only_defined_globals():
+    """Every global a function of bench.py reads is defined at module level or is a builtin (the
+    GPU-only legs never run on the CPU, so a missing helper would otherwise surface on a GPU machine)."""
+    import builtins
+    import symtable
+    src = open(bench.__file__).read()
+    top = symtable.symtable(src, bench.__file__, "exec")
+    missing = []
+
+    def walk(t):
+        for ch in t.get_children():
+            if ch.get_type() == "function":
+                for sym in ch.get_symbols():
+                    if sym.is_global() and sym.is_referenced() and not hasattr(bench, sym.get_name()) \
+                            and not hasattr(builtins, sym.get_name()):
+                        missing.append((ch.get_name(), sym.get_name()))
+            walk(ch)
+
+    walk(top)
+    assert not missing, missing

@@ -49,10 +49,7 @@ def test_warm_start_prediction_beats_cold_profile():
     s = torch.cuda.Stream()
 
     def runs(n, seed):
-        out = workloads.warmstart2d(n, seed)
-        for w in out:                       # a coarse mesh so the test stays short
-            w.mesh = workloads.Mesh(xb=np.linspace(0, 2, 9), yb=np.linspace(0, 1, 5), order=6)
-        return out
+        return workloads.warmstart2d(n, seed, 8, 4, 6)   # a coarse mesh so the test stays short
 
     train, test = runs(192, 101), runs(24, 202)
     f_tr, y_tr, _ = warmstart.generate(train, tol=0.0, max_steps=3000, check_every=3000, stream=s.cuda_stream)
@@ -80,10 +77,7 @@ def test_warm_start_saves_steps_to_the_equilibrium():
     s = torch.cuda.Stream()
 
     def runs(n, seed):
-        out = workloads.warmstart2d(n, seed)
-        for w in out:
-            w.mesh = workloads.Mesh(xb=np.linspace(0, 2, 9), yb=np.linspace(0, 1, 5), order=6)
-        return warmstart.equilibrium_runs(out)
+        return warmstart.equilibrium_runs(workloads.warmstart2d(n, seed, 8, 4, 6))
 
     tol, cap = 1e-3, 20000
     train, test = runs(256, 101), runs(24, 202)

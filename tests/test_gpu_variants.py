@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 FP32_VARIANTS = [(native.PF_GEMM_TC, 1), (native.PF_GEMM_PLANE, 1), (native.PF_GEMM_SIMT32, 0),
                  (native.PF_GEMM_SIMT32, 1), (native.PF_GEMM_SIMT64, 1), (native.PF_GEMM_SIMT32X64, 0),
                  (native.PF_GEMM_PIPE64, 0), (native.PF_GEMM_PIPE32, 1), (native.PF_GEMM_PIPE32X64, 0),
-                 (native.PF_GEMM_CLUSTER4, 1), (native.PF_GEMM_CLUSTER2, 1)]
+                 (native.PF_GEMM_CLUSTER4, 1), (native.PF_GEMM_CLUSTER2, 1), (native.PF_GEMM_TC_HYBRID, 1)]
 SIMT = (native.PF_GEMM_SIMT32, native.PF_GEMM_SIMT64, native.PF_GEMM_SIMT32X64, native.PF_GEMM_PIPE64,
         native.PF_GEMM_PIPE32, native.PF_GEMM_PIPE32X64)
 
@@ -80,7 +80,8 @@ def test_set_variant_rejects_what_the_run_cannot_use():
     g64 = native.from_workload(wl, precision=native.PF_FP64)
     gs = native.from_workload(wl, precision=native.PF_MIXED_SIMT)
     for h, args in [(g64, (native.PF_GEMM_PLANE, True, 0)), (g64, (native.PF_GEMM_TC, True, 0)),
-                    (gs, (native.PF_GEMM_TC, True, 0)), (gs, (48, True, 0)), (gs, (native.PF_GEMM_SIMT32, True, 6))]:
+                    (g64, (native.PF_GEMM_TC_HYBRID, True, 0)), (gs, (native.PF_GEMM_TC, True, 0)),
+                    (gs, (native.PF_GEMM_TC_HYBRID, True, 0)), (gs, (48, True, 0)), (gs, (native.PF_GEMM_SIMT32, True, 6))]:
         with pytest.raises(native.PfError) as e:
             h.set_variant(*args)
         assert e.value.code == native.PF_EINVAL
@@ -128,7 +129,7 @@ def test_batch_plane_variant_matches_oracle(gemm):
 @pytest.mark.parametrize("with_stream", [True, False])
 def test_autotune_advances_the_stated_steps_and_keeps_parity(with_stream):
     """pf_autotune times every variant (graph replays on a stream of its own, eager launches on the
-    legacy stream), advances the run by 15 (steps + 2) steps, and the run stays on the FP64 oracle."""
+    legacy stream), advances the run by 16 (steps + 2) steps, and the run stays on the FP64 oracle."""
     from oracle.runner import solver_of
     torch = pytest.importorskip("torch")
     wl = workloads.small3d(ex=4, ey=2, order=4, nz=8)
@@ -139,7 +140,7 @@ def test_autotune_advances_the_stated_steps_and_keeps_parity(with_stream):
     assert (choice // 1000) % 100 in (0, 4, 8, 16, 32) and choice // 100000 in (0, 1)
     g.step(3)
     ora = solver_of(wl)
-    for _ in range(1 + 15 * 3 + 3):
+    for _ in range(1 + 16 * 3 + 3):
         ora.step()
     errs = rel_errors(g.get(ALL), oracle_fields(ora))
     g.close()
@@ -168,8 +169,8 @@ def test_fp64_cuda_core_variants_agree_bit_for_bit(nz):
                 assert np.array_equal(f[k], ref[k]), (gemm, fuse_y, k)
 
 
-@pytest.mark.parametrize("gemm", [native.PF_GEMM_TC, native.PF_GEMM_CLUSTER4, native.PF_GEMM_PLANE,
-                                  native.PF_GEMM_PIPE32])
+@pytest.mark.parametrize("gemm", [native.PF_GEMM_TC, native.PF_GEMM_TC_HYBRID, native.PF_GEMM_CLUSTER4,
+                                  native.PF_GEMM_PLANE, native.PF_GEMM_PIPE32])
 def test_variant_graph_replay_is_bit_identical(gemm):
     """A pinned variant replayed from the captured graphs gives the bits of eager launches."""
     torch = pytest.importorskip("torch")

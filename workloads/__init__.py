@@ -344,10 +344,11 @@ def eval_on_grid(fn: Callable, x: np.ndarray, y: np.ndarray, z: Optional[np.ndar
     return np.ascontiguousarray(fn(X, Y, Z), dtype=np.float64)
 
 
-def warmstart2d(n: int, seed: int) -> List[Workload]:
-    """Runs for the learned warm start: one fixed mesh (16x8 elements, order 8) so that only the
-    voltage V ~ U(0,3), the permittivity ratio ~ logU(2,20) and the drop radius ~ U(0.15,0.35)
-    (drop centred on the wall, hence its volume) vary; eta = 0.02, dt = 1e-4."""
+def warmstart2d(n: int, seed: int, ex: int = 16, ey: int = 8, order: int = 8) -> List[Workload]:
+    """Runs for the learned warm start: one fixed mesh (ex x ey elements on [0,2] x [0,1], default
+    16x8 of order 8) so that only the voltage V ~ U(0,3), the permittivity ratio ~ logU(2,20) and
+    the drop radius ~ U(0.15,0.35) (drop centred on the wall, hence its volume) vary; eta = 0.02,
+    dt = 1e-4."""
     rng = np.random.default_rng(seed)
     eta = 0.02
     out = []
@@ -362,7 +363,7 @@ def warmstart2d(n: int, seed: int) -> List[Workload]:
 
         out.append(Workload(
             name=f"warmstart2d_{seed}_{i}",
-            mesh=Mesh(xb=np.linspace(0.0, 2.0, 17), yb=np.linspace(0.0, 1.0, 9), order=8),
+            mesh=Mesh(xb=np.linspace(0.0, 2.0, ex + 1), yb=np.linspace(0.0, 1.0, ey + 1), order=order),
             fluid=Fluid(rho1=1.0, rho2=1.0, mu1=1.0, mu2=1.0, eps1=eps_ratio, eps2=1.0,
                         sigma=1.0, eta=eta, gamma1=1e-4),
             vbc=VoltageBC(BC_DIRICHLET, BC_DIRICHLET, v_bottom=v, v_top=0.0),
