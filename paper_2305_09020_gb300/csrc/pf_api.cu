@@ -233,7 +233,10 @@ struct Engine {
 #ifndef PF_TC_SLICES_PER_GROUP
 #define PF_TC_SLICES_PER_GROUP 1
 #endif
-    int tc_group = PF_TC_SLICES_PER_GROUP;   // 8-wide K slices per TMEM accumulation group (1, 2 or 4)
+#ifndef PF_TC_HYBRID_GROUP
+#define PF_TC_HYBRID_GROUP 4
+#endif
+    int tc_group = PF_TC_SLICES_PER_GROUP;   // 8-wide K slices per TMEM accumulation group
     int tc_stall = 0;                 // test hook: the next tensor-core launch reports a time-out
     unsigned long long tc_wait_ns = 1000000000ull;   // bound of every wait (1 s)
     unsigned long long tc_wait_ns_next = 0;          // the test hook's bound
@@ -824,7 +827,7 @@ struct Engine {
     void set_gemm(int code) {
         use_tc = code == 0 || code == 8;
         tc_hybrid = code == 8;
-        tc_group = code == 8 ? 4 : PF_TC_SLICES_PER_GROUP;
+        tc_group = code == 8 ? PF_TC_HYBRID_GROUP : PF_TC_SLICES_PER_GROUP;
         fuse_plane = code == 1;
         cluster = code == 6 ? 4 : code == 7 ? 2 : 0;
         simt_tile = (code == 32 || code == 64 || (code >= 2 && code <= 5)) ? code : code == 8 ? 3 : 0;

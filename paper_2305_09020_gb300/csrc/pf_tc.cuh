@@ -51,7 +51,8 @@ struct TcArgs {
     int BNlast;               // width of the last column tile (multiple of 16, <= BN)
     int ntn;                  // column tiles
     int nchunk;               // K chunks of 32 (Kpad / 32)
-    int gs;                   // 8-wide K slices per TMEM accumulation group: 1, 2 or 4
+    int gs;                   // 8-wide K slices per TMEM accumulation group (>= 1; a tile's last
+                              // group may be shorter)
     int nr;                   // TMEM regions in the ring (nr BN <= tmem_cols, nr <= TC_MAXR)
     int stages;               // shared-memory stages
     int tmem_cols;            // allocated TMEM columns (power of two >= 2 BN)
@@ -261,7 +262,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
                 const uint32_t aH = sb, aL = sb + ABYTES, bH = sb + 2 * ABYTES, bL = bH + BBYTES;
                 for (int kk = 0; kk < TC_KC / 8; ++kk) {
-                    const bool first = kk % g.gs == 0, last = kk % g.gs == g.gs - 1;
+                    // groups of gs slices counted from the tile's first slice; the tile's last
+                    // slice closes its group
+                    const int sk = c * (TC_KC / 8) + kk;
+                    const bool first = sk % g.gs == 0;
+                    const bool last = sk % g.gs == g.gs - 1 || (c == nchunk - 1 && kk == TC_KC / 8 - 1);
                     const int r = grp % NR;
                     if (first) {
                         if (!mbar_wait(b_rempty + 8 * r, (uint32_t)(((grp / NR) & 1) ^ 1), abort_flag, g.wait_ns)) {
@@ -300,14 +305,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float acc[TC_MAXH];
 #pragma unroll
         for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
-        int grp = 0, c = 0, t = blockIdx.x;   // c, t: chunk and tile of q - 1
+        const int ngrp = ((TC_KC / 8) * nchunk + g.gs - 1) / g.gs;   // groups per tile
+        int grp = 0;
         bool ok = true;
-        for (int q = 1; q <= Q && ok; ++q) {
-            // the groups of chunk q - 1, in K order, into the registers
-            const int cd = c, td = t;
-            if (++c == nchunk) { c = 0; t += gridDim.x; }
+        for (int it = 0; it < my_tiles && ok; ++it) {
+            // the tile's groups, in K order, into the registers
+            const int td = (int)blockIdx.x + it * (int)gridDim.x;
             const int hbn = ((td % g.ntn == g.ntn - 1) ? g.BNlast : BN) >> 1;   // columns per thread
-            for (int gi = 0; gi < (TC_KC / 8) / g.gs; ++gi) {
+            for (int gi = 0; gi < ngrp; ++gi) {
                 const int r = grp % NR;
                 if (!mbar_wait(b_rfull + 8 * r, (uint32_t)((grp / NR) & 1), abort_flag, g.wait_ns)) {
                     ok = false;
@@ -331,7 +336,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ++grp;
             }
             if (!ok) break;
-            if (cd != nchunk - 1) continue;
             // ---- epilogue of tile td ------------------------------------------------------------
             const int mt = td / g.ntn, nt = td - mt * g.ntn;
             const int m = mt * TC_BM + quarter * 32 + lane;
