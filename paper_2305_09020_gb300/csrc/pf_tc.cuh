@@ -40,6 +40,8 @@ constexpr int TC_THREADS = 12 * 32;                 // warpgroup 2: producer, MM
 // register split (setmaxnreg): the launch holds 384 x 168 = 64512 registers; warpgroup 2 gives
 // back down to 72 a thread and the epilogue warpgroups take 216: 256 x 216 + 128 x 72 = 64512
 constexpr int TC_REG_EPI = 216, TC_REG_AUX = 72;
+static_assert(TC_EPI_WARPS * 32 * TC_REG_EPI + (TC_THREADS - TC_EPI_WARPS * 32) * TC_REG_AUX <= 65536,
+              "the setmaxnreg split must fit the launch's registers");
 constexpr int TC_MAXH = 64;                         // accumulator columns per thread: BN <= 128
 constexpr int TC_MAXR = 8;                          // TMEM regions in the ring at most
 constexpr int TC_ERR_TIMEOUT = 1;                   // error word: a bounded wait gave up
@@ -71,10 +73,11 @@ struct TcArgs {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// round to the nearest TF32 value, ties away from zero, in integer arithmetic (full-rate ALU ops):
+// add half a unit of the 10-bit mantissa's last place to the magnitude bits and clear the 13 low
+// bits; a carry moves into the exponent as rounding requires; non-finite inputs stay non-finite
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // K-major, 128-byte swizzle, 8-row atoms of 1024 bytes: matrix descriptor of a tile at addr
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!ok) fail();
     } else {
         // ---- split A into TF32 head (in place) and tail (warps 10-11: 64 floats a thread) -----
-        const int ct = tid - (TC_EPI_WARPS + 2) * 32;   // 0..63
+        const int ct = tid - (TC_EPI_WARPS + 2) * 32;   // 0 .. 32 TC_CONV_WARPS - 1
         int s = 0;
         uint32_t ph = 0;
         for (int q = 0; q < Q; ++q) {
@@ -405,8 +408,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             unsigned char *sa = base + (size_t)s * STAGE;
 #pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const uint32_t off = (uint32_t)(16 * (ct + 64 * i));
+            for (int i = ct; i < (int)(ABYTES / 16); i += 32 * TC_CONV_WARPS) {
+                const uint32_t off = (uint32_t)(16 * i);
                 const float4 x = *(const float4 *)(sa + off);
                 float4 h, l;
                 h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
