@@ -555,7 +555,8 @@ def main():
             "config": {"workload": WORKLOADS[args.workload] + (f" (Nz overridden to {nz})" if args.nz > 0 else ""),
                        "dof_per_field": dof, "fourier_coeffs_per_field": nx * ny * (nz // 2 + 1),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
-                       "fdm_gemm": {0: "tcgen05 3xTF32", 1: "whole solve per plane in shared memory (SIMT)",
+                       "fdm_gemm": {0: "tcgen05 3xTF32 (psi, phi: 2-slice TMEM groups, V, P, u: 8-slice groups; correction "
+                                       "products in a per-tile region)", 1: "whole solve per plane in shared memory (SIMT)",
                                     2: "SIMT 32x64 tiles", 3: "SIMT 64x64 tiles, cp.async pipeline",
                                     4: "SIMT 32x32 tiles, cp.async pipeline", 5: "SIMT 32x64 tiles, cp.async pipeline",
                                     6: "whole solve per plane on a 4-block cluster (SIMT, distributed shared memory)",

@@ -294,6 +294,21 @@ int pf_autotune(pf_handle *h, int steps, int *choice, double *ms_per_step);
  * large). */
 int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile);
 
+/* Accumulation of the 3xTF32 tensor-core transforms (the constant eigenbasis products of the
+ * Remark after Algorithm 2) for variant gemm (PF_GEMM_TC or PF_GEMM_TC_HYBRID) and solve family
+ * (0: the psi and phi solves of the split Cahn-Hilliard step, eq. 44, and with electrode patches
+ * the potential solves, whose capacitance correction subtracts two solutions; 1: the other V, P
+ * and u solves):
+ * every `slices` 8-wide K slices (1..64) accumulate in a tensor-memory region of their own,
+ * drained into FP32 registers with rounding to nearest; sep = 1 chains the two small correction
+ * products of a whole output tile in a separate region (drained once per tile), so that a group's
+ * region holds only the main products.  The tensor core truncates its FP32 sums: longer groups
+ * run faster and lose more digits.  Defaults: PF_GEMM_TC 2 slices with sep for psi, phi and 8
+ * with sep for the others; PF_GEMM_TC_HYBRID (psi, phi on CUDA cores) 4 without sep.  Applies
+ * from the next step (captured graphs are dropped).  PF_EINVAL when h is not a PF_MIXED run or a
+ * value is outside these sets. */
+int pf_set_tc_accum(pf_handle *h, int gemm, int family, int slices, int sep);
+
 /* Test hook of the failure detection (Sec. 3 has no counterpart): the next tensor-core transform
  * launch of h waits on a device barrier that nothing arrives at, gives up after wait_ns
  * nanoseconds (0 < wait_ns <= 1e10), records the time-out in the handle's error word and returns

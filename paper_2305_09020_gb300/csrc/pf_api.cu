@@ -230,13 +230,15 @@ struct Engine {
     };
     std::vector<TcB> tcb;
     bool use_tc = false;
-#ifndef PF_TC_SLICES_PER_GROUP
-#define PF_TC_SLICES_PER_GROUP 1
-#endif
-#ifndef PF_TC_HYBRID_GROUP
-#define PF_TC_HYBRID_GROUP 4
-#endif
-    int tc_group = PF_TC_SLICES_PER_GROUP;   // 8-wide K slices per TMEM accumulation group
+    // TMEM accumulation of the tensor-core transforms, per variant (index 0: PF_GEMM_TC, 1:
+    // PF_GEMM_TC_HYBRID) and solve family (index 0: the psi and phi solves of the Cahn-Hilliard
+    // pair, whose errors feed phi directly; 1: V, P and u): 8-wide K slices per group, and whether
+    // the correction products chain in a per-tile region of their own (pf::TcArgs::sep).  The
+    // hybrid runs the psi and phi solves on CUDA cores, so its index-0 entries are unused.
+    int tc_gs[2][2] = {{2, 8}, {4, 4}};
+    int tc_sepv[2][2] = {{1, 1}, {0, 0}};
+    int tc_group = 2;                 // of the solve being launched
+    int tc_sep = 1;
     int tc_stall = 0;                 // test hook: the next tensor-core launch reports a time-out
     unsigned long long tc_wait_ns = 1000000000ull;   // bound of every wait (1 s)
     unsigned long long tc_wait_ns_next = 0;          // the test hook's bound
@@ -567,7 +569,9 @@ struct Engine {
         if (rows >= (1ll << 31)) throw CudaError{cudaErrorInvalidValue, "tensor-core transform with 2^31 rows"};
         a.M = (int)rows; a.N = tb->N; a.BN = tb->BN; a.BNlast = tb->BNlast; a.ntn = tb->ntn;
         a.nchunk = tb->Kpad / pf::TC_KC;
-        a.gs = tc_group; a.nr = tb->nr; a.stages = tb->stages; a.tmem_cols = tb->tmem_cols;
+        a.gs = tc_group; a.stages = tb->stages; a.tmem_cols = tb->tmem_cols;
+        a.sep = tc_sep;
+        a.nr = tc_sep ? std::min(pf::TC_MAXR, tb->tmem_cols / tb->BN - 2) : tb->nr;
         a.ntiles = (int)((rows + pf::TC_BM - 1) / pf::TC_BM * tb->ntn);
         a.R = R; a.store = store; a.ldc = ldc; a.ldr = ldr;
         a.lamN = reinterpret_cast<const float *>(lamN);
@@ -595,6 +599,11 @@ struct Engine {
     // fast-diagonalisation solve on the tensor cores: the four transforms of fdm() with the y
     // intermediates at row pitch nyp (16-byte rows for TMA)
     void fdm_tc(const T *rhs, T *out, int bcset, const T *sh, long long P, T *minus_m_out, const T *face) {
+        // the psi, phi pair, and with electrode patches the potential (whose capacitance correction
+        // subtracts two solves), take the accurate family
+        const int fam = (bcset == PF_BCSET_NN || (bcset == PF_BCSET_V && hs.patch)) ? 0 : 1;
+        tc_group = tc_gs[tc_hybrid ? 1 : 0][fam];
+        tc_sep = tc_sepv[tc_hybrid ? 1 : 0][fam];
         // x: W1[p][x][y] (pitch nyp) = (rhs[p][y][:] Sx)^T
         gemm_tc(rhs, nx, Sx, W1, P * ny, ny, 1, 0, nyp, nullptr, nullptr, nullptr, 1);
         // y with the eigenvalue division: W2[p][x][:] = (W1[p][x][:] Sy) / (Ly + Lx + shift)
@@ -827,7 +836,6 @@ struct Engine {
     void set_gemm(int code) {
         use_tc = code == 0 || code == 8;
         tc_hybrid = code == 8;
-        tc_group = code == 8 ? PF_TC_HYBRID_GROUP : PF_TC_SLICES_PER_GROUP;
         fuse_plane = code == 1;
         cluster = code == 6 ? 4 : code == 7 ? 2 : 0;
         simt_tile = (code == 32 || code == 64 || (code >= 2 && code <= 5)) ? code : code == 8 ? 3 : 0;
@@ -1007,7 +1015,18 @@ struct Engine {
         const long long tot = N;
         prof->begin(PF_KC_EFIELD, st);
         by_order([&](auto kc) {
-            pf::k_efield<T, decltype(kc)::value><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(geo(), Vf, Ex, Ey);
+            constexpr int KC = decltype(kc)::value;
+            const size_t rows_smem = (size_t)2 * (K + 1) * nx * sizeof(float);
+            if constexpr (KC > 0 && sizeof(T) == 4) {
+                if (rows_smem <= 48 * 1024) {   // element rows and columns per thread (FP32)
+                    pf::DTab<KC> t;
+                    for (int i = 0; i < (KC + 1) * (KC + 1); ++i) t.d[i] = (float)hs.D[i];
+                    for (int i = 0; i <= KC; ++i) t.w[i] = (float)hs.w[i];
+                    pf::k_efield_rows<KC><<<dim3(ey, nz), 256, rows_smem, st>>>(geo(), t, Vf, Ex, Ey);
+                    return;
+                }
+            }
+            pf::k_efield<T, KC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(geo(), Vf, Ex, Ey);
         });
         check_launch();
         prof->end(st);
@@ -1930,6 +1949,26 @@ extern "C" int pf_set_variant(pf_handle *h, int gemm, int fuse_y, int tile) {
             h->err = "pf_set_variant: variant not available for this run";
             return PF_EINVAL;
         }
+    } catch (const CudaError &e) {
+        return cuda_fail(h, e);
+    }
+    return PF_OK;
+}
+
+extern "C" int pf_set_tc_accum(pf_handle *h, int gemm, int family, int slices, int sep) {
+    if (!h) return PF_EINVAL;
+    if (gemm != PF_GEMM_TC && gemm != PF_GEMM_TC_HYBRID) return fail(h, PF_EINVAL, "gemm must be PF_GEMM_TC or PF_GEMM_TC_HYBRID");
+    if (family != 0 && family != 1) return fail(h, PF_EINVAL, "family 0 (psi, phi solves) or 1 (V, P, u solves)");
+    if (slices < 1 || slices > 64 || (sep != 0 && sep != 1)) return fail(h, PF_EINVAL, "slices in [1, 64], sep 0 or 1");
+    if (!h->e32) return fail(h, PF_EINVAL, "tensor-core transforms run in PF_MIXED only");
+    try {
+        PF_CU(cudaStreamSynchronize(h->st));
+        auto &E = *h->e32;
+        const int v = gemm == PF_GEMM_TC_HYBRID ? 1 : 0;
+        E.tc_gs[v][family] = slices;
+        E.tc_sepv[v][family] = sep;
+        for (int c = 0; c < 2; ++c)
+            if (E.graph[c]) { cudaGraphExecDestroy(E.graph[c]); E.graph[c] = nullptr; }
     } catch (const CudaError &e) {
         return cuda_fail(h, e);
     }

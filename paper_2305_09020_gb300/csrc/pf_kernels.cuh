@@ -297,6 +297,93 @@ __global__ void k_efield(Geo<T> G_, const T *__restrict__ V, T *__restrict__ Ex,
     Ey[gid] = sy / G.My[i];
 }
 
+// The same E_x, E_y (eq. 55 / 78) for FP32 runs of a compiled order: one block per element row
+// e_y and plane.  A thread takes a whole element segment of a node row (x) or a whole element
+// column (y), so that the derivative weights are the same in every thread and come from the
+// kernel's parameters: K + 1 (2K + 2 at element boundaries) values per K nodes instead of up to
+// 4(K + 1) loads per node.  The node rows of the block are staged in shared memory; E_x goes
+// through shared memory so that its global stores coalesce.  Same sums in the same order as
+// k_efield.
+template <int KC>
+struct DTab {
+    float d[(KC + 1) * (KC + 1)];   // D[a (K+1) + m]
+    float w[KC + 1];                // GLL weights
+};
+
+template <int KC>
+__global__ void __launch_bounds__(256) k_efield_rows(Geo<float> G_, DTab<KC> t, const float *__restrict__ V,
+                                                     float *__restrict__ Ex, float *__restrict__ Ey) {
+    constexpr int K = KC, P = KC + 1;
+    const Geo<float> G = fixed_order<KC>(G_);
+    extern __shared__ __align__(16) unsigned char pf_smem_raw[];
+    float *sV = reinterpret_cast<float *>(pf_smem_raw);
+    const int nx = G.nx, ey = blockIdx.x, r0 = ey * K;
+    const int nr = (ey == G.ey - 1) ? K + 1 : K;   // node rows r0 .. r0 + nr - 1 (the top one once)
+    float *sE = sV + P * nx;
+    const float *Vp = V + (long long)blockIdx.y * G.n2;
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) sV[i] = Vp[(long long)r0 * nx + i];
+    // y: one element column per thread (element e_y, and e_y - 1 for the shared bottom row)
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        float c[P], cl[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) c[m] = Vp[(long long)(r0 + m) * nx + j];
+        if (ey > 0) {
+#pragma unroll
+            for (int m = 0; m < P; ++m) cl[m] = Vp[(long long)(r0 - K + m) * nx + j];
+        }
+        float *Eyp = Ey + (long long)blockIdx.y * G.n2 + j;
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            if (b == K && ey != G.ey - 1) break;
+            float sy = 0.f;
+            if (b == 0 && ey > 0) {
+                float s = 0.f;
+#pragma unroll
+                for (int m = 0; m < P; ++m) s += t.d[K * P + m] * cl[m];
+                sy += t.w[K] * s;
+            }
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < P; ++m) s += t.d[b * P + m] * c[m];
+            sy += t.w[b] * s;
+            Eyp[(long long)(r0 + b) * nx] = sy / G.My[r0 + b];
+        }
+    }
+    __syncthreads();
+    // x: one element segment of a node row per thread (the element, and its left neighbour for
+    // the shared node a = 0; x is periodic)
+    for (int it = threadIdx.x; it < nr * G.ex; it += blockDim.x) {
+        const int r = it / G.ex, e = it - r * G.ex;
+        const float *row = sV + r * nx;
+        const int el = e == 0 ? G.ex - 1 : e - 1;
+        float v[P], vl[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            int cc = e * K + m;
+            if (cc >= nx) cc -= nx;
+            v[m] = row[cc];
+            vl[m] = row[el * K + m < nx ? el * K + m : el * K + m - nx];
+        }
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < P; ++m) s += t.d[a * P + m] * v[m];
+            float sx = t.w[a] * s;
+            if (a == 0) {
+                float sl = 0.f;
+#pragma unroll
+                for (int m = 0; m < P; ++m) sl += t.d[K * P + m] * vl[m];
+                sx += t.w[K] * sl;
+            }
+            sE[r * nx + e * K + a] = sx / G.Mx[e * K + a];
+        }
+    }
+    __syncthreads();
+    float *Exp = Ex + (long long)blockIdx.y * G.n2 + (long long)r0 * nx;
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) Exp[i] = sE[i];
+}
+
 // ---- eq. 56 / 75: psi right-hand side ----------------------------------------------------
 // Q1 = (-u* . grad phi* + phi_hat/dt)/(lambda gamma1) (element-local),
 // Q2 = h(phi*) - (S/eta^2) phi* - eps'(phi*)/(2 lambda) |E|^2 (nodal, written to Q2n),

@@ -18,11 +18,17 @@
 // The tensor core's FP32 accumulation is not rounded to nearest, and the eigenvector sums cancel
 // heavily, so a chain of MMAs in one accumulator loses digits (chunks of 32 in one region: phi of
 // the 2D droplet drifted 4x further from the oracle in 50 steps than with one region per slice).
-// Each group of `gs` 8-wide K slices (default 1) therefore accumulates into its own TMEM region,
-// taken from a ring of NR = 512 / BN regions: the MMAs of later groups run while warps 0-7 add the
-// finished groups into FP32 registers with round-to-nearest, in K order.  Within a slice the two
-// small correction products go first.  Every mbarrier wait is bounded (globaltimer); on time-out
-// the kernel records an error word, lets its own copies and MMAs finish (bounded), frees its
+// Each group of `gs` 8-wide K slices therefore accumulates into its own TMEM region, taken from a
+// ring of NR regions: the MMAs of later groups run while warps 0-7 add the finished groups into
+// FP32 registers with round-to-nearest, in K order.  Two layouts (`sep`):
+//   sep = 0  a group's region takes all three products of its slices (the two small correction
+//            products first); every product added into a running sum is truncated against it
+//   sep = 1  the main products hi*hi go to the group's region; the correction products of the
+//            whole tile (2^-11 of the main term, so their truncations are 2^-11 smaller) chain into
+//            one region per tile (two, alternating between tiles), drained once per tile: per
+//            slice one truncation against a running main-term sum, as with sep = 0 and one slice
+//            per group, at a fraction of the drains
+// Every mbarrier wait is bounded (counted in SM cycles); on time-out the kernel records an error word, lets its own copies and MMAs finish (bounded), frees its
 // tensor memory and returns.
 #pragma once
 
@@ -55,7 +61,8 @@ struct TcArgs {
     int nchunk;               // K chunks of 32 (Kpad / 32)
     int gs;                   // 8-wide K slices per TMEM accumulation group (>= 1; a tile's last
                               // group may be shorter)
-    int nr;                   // TMEM regions in the ring (nr BN <= tmem_cols, nr <= TC_MAXR)
+    int nr;                   // TMEM regions in the ring (nr <= TC_MAXR; (nr + 2 sep) BN <= tmem_cols)
+    int sep;                  // 1: correction products in a per-tile region of their own (above)
     int stages;               // shared-memory stages
     int tmem_cols;            // allocated TMEM columns (power of two >= 2 BN)
     int ntiles;               // row tiles x column tiles
@@ -169,6 +176,48 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// the hbn (<= TC_MAXH, a multiple of 8) accumulator columns of this thread's lane at taddr into
+// v: 32-column loads where whole, 8-column loads for the rest; the caller waits (wait::ld)
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int hbn, float *v) {
+#pragma unroll
+    for (int j0 = 0; j0 < TC_MAXH; j0 += 32) {
+        if (j0 + 32 <= hbn) {
+            tmem_ld32(taddr + (uint32_t)j0, v + j0);
+        } else {
+#pragma unroll
+            for (int j1 = j0; j1 < j0 + 32; j1 += 8)
+                if (j1 < hbn) tmem_ld8(taddr + (uint32_t)j1, v + j1);
+        }
+    }
+}
+
+// acc[j] += v[j] for j < hbn, two lanes of FP32 per instruction (round to nearest)
+__device__ __forceinline__ void add_cols(float *acc, const float *v, int hbn) {
+#pragma unroll
+    for (int j = 0; j < TC_MAXH; j += 2)
+        if (j < hbn) {
+            unsigned long long x, y, z;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(acc[j]), "f"(acc[j + 1]));
+            asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(v[j]), "f"(v[j + 1]));
+            asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[j]), "=f"(acc[j + 1]) : "l"(z));
+        }
+}
+
 #ifndef PF_TC_HELPERS_ONLY   // translation units that only need the helpers above
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
@@ -180,11 +229,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t STAGE = 2 * ABYTES + 2 * BBYTES;
     uint64_t *bars = (uint64_t *)(base + (size_t)S * STAGE);
     // barriers: full[S] (TMA landed), conv[S] (A split), empty[S] (MMAs done with the stage),
-    // rfull[TC_MAXR] (a group's MMAs done), rempty[TC_MAXR] (a group drained), stall
-    const int NR = g.nr;
+    // rfull[TC_MAXR] (a group's MMAs done), rempty[TC_MAXR] (a group drained), stall,
+    // cfull[2] (a tile's correction products done), cempty[2] (drained)
+    const int NR = g.nr, SEP = g.sep;
     const uint32_t b_full = smem_u32(bars), b_conv = b_full + 8 * S, b_empty = b_conv + 8 * S;
     const uint32_t b_rfull = b_empty + 8 * S, b_rempty = b_rfull + 8 * TC_MAXR, b_stall = b_rempty + 8 * TC_MAXR;
-    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 2 * TC_MAXR + 1);
+    const uint32_t b_cfull = b_stall + 8, b_cempty = b_cfull + 16;
+    const uint32_t rbase = SEP ? 2u * (uint32_t)BN : 0u;   // column of the ring's first region
+    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 2 * TC_MAXR + 5);
     volatile int *abort_flag = (volatile int *)(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -199,6 +251,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(b_rempty + 8 * r, TC_EPI_WARPS);
         }
         mbar_init(b_stall, 1);
+        for (int c = 0; c < 2; ++c) {
+            mbar_init(b_cfull + 8 * c, 1);
+            mbar_init(b_cempty + 8 * c, TC_EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -232,11 +288,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmBh) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmBl) : "memory");
-            int issued = 0, s = 0, c = 0, t = blockIdx.x;
+            // tile coordinates kept as running counters (no division per chunk)
+            const int ntn = g.ntn, gstep = (int)gridDim.x % ntn, mstep = (int)gridDim.x / ntn;
+            int issued = 0, s = 0, c = 0, mt = (int)blockIdx.x / ntn, nt = (int)blockIdx.x % ntn;
             uint32_t ph = 0;
             for (int q = 0; q < Q; ++q) {
                 if (!mbar_wait(b_empty + 8 * s, ph ^ 1u, abort_flag, g.wait_ns)) { fail(); break; }
-                const int mt = t / g.ntn, nt = t - mt * g.ntn;
                 const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
                 mbar_expect_tx(b_full + 8 * s, STAGE - ABYTES);   // A, Bt hi, Bt lo (A's lo buffer is ours)
                 tma_load_2d(sb, &tmA, c * TC_KC, mt * TC_BM, b_full + 8 * s);
@@ -244,7 +301,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sb + 2 * ABYTES + BBYTES, &tmBl, c * TC_KC, nt * BN, b_full + 8 * s);
                 issued = q + 1;
                 if (++s == S) { s = 0; ph ^= 1u; }
-                if (++c == nchunk) { c = 0; t += gridDim.x; }
+                if (++c == nchunk) {
+                    c = 0;
+                    mt += mstep;
+                    nt += gstep;
+                    if (nt >= ntn) { nt -= ntn; ++mt; }
+                }
             }
             // our copies still in flight (only after an abort) finish before the CTA leaves
             for (int q = issued - 1; q >= 0 && q >= issued - S; --q)
@@ -253,47 +315,77 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else if (warp == TC_EPI_WARPS + 1) {
         // ---- MMA issuer -----------------------------------------------------------------------
+        // One thread issues every MMA, so its loop is latency-bound: no divisions, descriptors
+        // advanced by constants, group and ring positions kept as running counters.
         if (lane == 0) {
             const uint32_t idesc_full = idesc_tf32(TC_BM, BN), idesc_last = idesc_tf32(TC_BM, g.BNlast);
-            int grp = 0, s = 0, c = 0, t = blockIdx.x;
-            uint32_t ph = 0;
+            // shared-memory descriptors advance in 16-byte units: stage, operand and K-slice offsets
+            const uint64_t dbase = sdesc_sw128(smem_u32(base));
+            const uint64_t dstage = STAGE >> 4, daL = ABYTES >> 4, dbH = (2 * ABYTES) >> 4,
+                           dbL = (2 * ABYTES + BBYTES) >> 4;
+            const int gs = g.gs, ntn = g.ntn, gstep = (int)gridDim.x % ntn;
+            int nt = (int)blockIdx.x % ntn;   // column tile of the current tile
+            int s = 0, c = 0, it = 0, r = 0, ing = 0;   // stage, chunk, tile, ring region, slice in group
+            uint32_t ph = 0, rph = 0;                   // stage and ring phases
+            uint64_t ds = dbase;
             bool ok = true;
             for (int q = 0; q < Q && ok; ++q) {
                 if (!mbar_wait(b_conv + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
+                // sep: the tile's correction region (it & 1) is free once its previous tile is drained
+                if (SEP && c == 0 &&
+                    !mbar_wait(b_cempty + 8 * (it & 1), (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, g.wait_ns)) {
+                    fail();
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = (t % g.ntn == g.ntn - 1) ? idesc_last : idesc_full;
-                const uint32_t sb = smem_u32(base + (size_t)s * STAGE);
-                const uint32_t aH = sb, aL = sb + ABYTES, bH = sb + 2 * ABYTES, bL = bH + BBYTES;
+                const uint32_t idesc = nt == ntn - 1 ? idesc_last : idesc_full;
+                const uint32_t dcor = tmem + (uint32_t)((it & 1) * BN);
+                const bool last_chunk = c == nchunk - 1;
+#pragma unroll
                 for (int kk = 0; kk < TC_KC / 8; ++kk) {
                     // groups of gs slices counted from the tile's first slice; the tile's last
                     // slice closes its group
-                    const int sk = c * (TC_KC / 8) + kk;
-                    const bool first = sk % g.gs == 0;
-                    const bool last = sk % g.gs == g.gs - 1 || (c == nchunk - 1 && kk == TC_KC / 8 - 1);
-                    const int r = grp % NR;
+                    const bool first = ing == 0;
+                    const bool last = ing == gs - 1 || (last_chunk && kk == TC_KC / 8 - 1);
                     if (first) {
-                        if (!mbar_wait(b_rempty + 8 * r, (uint32_t)(((grp / NR) & 1) ^ 1), abort_flag, g.wait_ns)) {
+                        if (!mbar_wait(b_rempty + 8 * r, rph ^ 1u, abort_flag, g.wait_ns)) {
                             fail();
                             ok = false;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     }
-                    const uint32_t d = tmem + (uint32_t)(r * BN);
-                    const uint32_t o = (uint32_t)(kk * 32);
-                    // the two small correction products first, then the main term
-                    mma_tf32(d, sdesc_sw128(aL + o), sdesc_sw128(bH + o), idesc, first ? 0u : 1u);
-                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bL + o), idesc, 1u);
-                    mma_tf32(d, sdesc_sw128(aH + o), sdesc_sw128(bH + o), idesc, 1u);
+                    const uint32_t d = tmem + rbase + (uint32_t)(r * BN);
+                    const uint64_t o = ds + 2 * kk;     // this 8-wide K slice: 32 bytes further
+                    if (SEP) {   // correction products into the tile's region, the main one into the group's
+                        mma_tf32(dcor, o + daL, o + dbH, idesc, (c == 0 && kk == 0) ? 0u : 1u);
+                        mma_tf32(dcor, o, o + dbL, idesc, 1u);
+                        mma_tf32(d, o, o + dbH, idesc, first ? 0u : 1u);
+                    } else {     // the two small correction products first, then the main term
+                        mma_tf32(d, o + daL, o + dbH, idesc, first ? 0u : 1u);
+                        mma_tf32(d, o, o + dbL, idesc, 1u);
+                        mma_tf32(d, o, o + dbH, idesc, 1u);
+                    }
                     if (last) {
                         mma_commit(b_rfull + 8 * r);
-                        ++grp;
+                        ing = 0;
+                        if (++r == NR) { r = 0; rph ^= 1u; }
+                    } else {
+                        ++ing;
                     }
                 }
                 if (!ok) break;
+                if (SEP && last_chunk) {
+                    mma_commit(b_cfull + 8 * (it & 1));
+                    ++it;
+                }
                 mma_commit(b_empty + 8 * s);   // the stage is free once these MMAs have read it
-                if (++s == S) { s = 0; ph ^= 1u; }
-                if (++c == nchunk) { c = 0; t += gridDim.x; }
+                if (++s == S) { s = 0; ph ^= 1u; ds = dbase; } else { ds += dstage; }
+                if (++c == nchunk) {
+                    c = 0;
+                    nt += gstep;
+                    if (nt >= ntn) nt -= ntn;
+                }
             }
             // every MMA issued (also after an abort) finishes before the tensor memory is released:
             // one more commit, on the barrier the stall hook uses (idle on this path)
@@ -309,36 +401,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < TC_MAXH; ++j) acc[j] = 0.f;
         const int ngrp = ((TC_KC / 8) * nchunk + g.gs - 1) / g.gs;   // groups per tile
-        int grp = 0;
+        int r = 0;           // ring region of the next group, and its phase
+        uint32_t rph = 0;
         bool ok = true;
         for (int it = 0; it < my_tiles && ok; ++it) {
             // the tile's groups, in K order, into the registers
             const int td = (int)blockIdx.x + it * (int)gridDim.x;
             const int hbn = ((td % g.ntn == g.ntn - 1) ? g.BNlast : BN) >> 1;   // columns per thread
             for (int gi = 0; gi < ngrp; ++gi) {
-                const int r = grp % NR;
-                if (!mbar_wait(b_rfull + 8 * r, (uint32_t)((grp / NR) & 1), abort_flag, g.wait_ns)) {
+                if (!mbar_wait(b_rfull + 8 * r, rph, abort_flag, g.wait_ns)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * BN + half * hbn);
+                const uint32_t ta =
+                    tmem + ((uint32_t)(quarter * 32) << 16) + rbase + (uint32_t)(r * BN + half * hbn);
                 {   // every column of the group first, then one wait
                     float v[TC_MAXH];
-#pragma unroll
-                    for (int j0 = 0; j0 < TC_MAXH; j0 += 8)
-                        if (j0 < hbn) tmem_ld8(ta + (uint32_t)j0, v + j0);
+                    tmem_ld_cols(ta, hbn, v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < TC_MAXH; ++j)
-                        if (j < hbn) acc[j] += v[j];
+                    add_cols(acc, v, hbn);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_rempty + 8 * r);
-                ++grp;
+                if (++r == NR) { r = 0; rph ^= 1u; }
             }
             if (!ok) break;
+            if (SEP) {   // the tile's correction products, once
+                const int cr = it & 1;
+                if (!mbar_wait(b_cfull + 8 * cr, (uint32_t)((it >> 1) & 1), abort_flag, g.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cr * BN + half * hbn);
+                float v[TC_MAXH];
+                tmem_ld_cols(ta, hbn, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                add_cols(acc, v, hbn);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_cempty + 8 * cr);
+            }
             // ---- epilogue of tile td ------------------------------------------------------------
             const int mt = td / g.ntn, nt = td - mt * g.ntn;
             const int m = mt * TC_BM + quarter * 32 + lane;

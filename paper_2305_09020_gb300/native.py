@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
     L.pf_set_variant.argtypes = [c_void_p, c_int, c_int, c_int]
     L.pf_set_step.argtypes = [c_void_p, c_int, c_double]
     L.pf_measure_peaks.argtypes = [POINTER(c_double)]
+    L.pf_set_tc_accum.argtypes = [c_void_p, c_int, c_int, c_int, c_int]
     L.pf_debug_tc_stall.argtypes = [c_void_p, ctypes.c_ulonglong]
     L.pf_fdm_solve_static.argtypes = [c_int, c_int, c_int] + [c_void_p] * 10
     L.pf_batch_create.argtypes = [c_int, POINTER(PfMesh), POINTER(PfFluid), POINTER(PfVbc), POINTER(PfScheme),
@@ -273,6 +274,12 @@ class Solver:
     def set_step(self, nstep: int, t: float):
         """Restart bookkeeping: step count (BDF order of the next step) and time."""
         _check(load().pf_set_step(self._h, int(nstep), float(t)), self._h)
+
+    def set_tc_accum(self, gemm: int, family: int, slices: int, sep: int):
+        """Accumulation of the tensor-core transforms of variant gemm for a solve family (0: psi
+        and phi, 1: V, P, u): K slices per TMEM group, and whether the correction products chain
+        in a region of their own."""
+        _check(load().pf_set_tc_accum(self._h, int(gemm), int(family), int(slices), int(sep)), self._h)
 
     def debug_tc_stall(self, wait_ns: int):
         """Test hook: the next tensor-core transform launch reports a time-out after wait_ns."""

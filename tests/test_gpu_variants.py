@@ -186,3 +186,52 @@ def test_variant_graph_replay_is_bit_identical(gemm):
     b.close()
     for k in fa:
         assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.fixture(scope="module")
+def droplet2d_100():
+    """The FP64 oracle's 2D droplet after 50 and 100 steps."""
+    from oracle.runner import solver_of
+    wl = workloads.droplet2d()
+    ora = solver_of(wl)
+    out = {}
+    for n in range(1, 101):
+        ora.step()
+        if n in (50, 100):
+            out[n] = oracle_fields(ora)
+    return wl, out
+
+
+@pytest.mark.parametrize("gemm,acc", [(native.PF_GEMM_TC, None), (native.PF_GEMM_TC, ((1, 0), (1, 0))),
+                                      (native.PF_GEMM_TC, ((2, 1), (2, 1))), (native.PF_GEMM_TC_HYBRID, None),
+                                      (native.PF_GEMM_TC_HYBRID, ((4, 0), (8, 1)))])
+def test_tc_accumulation(droplet2d_100, gemm, acc):
+    """The tensor-core transforms with each accumulation layout (slices per TMEM group, correction
+    products in their own region, per solve family; None: the defaults) hold the mixed bars of the
+    2D droplet over 100 steps against the oracle: 5e-5 on V, phi, psi and 5e-4 on E, P, u."""
+    wl, ref = droplet2d_100
+    g = native.from_workload(wl, precision=native.PF_MIXED)
+    g.set_variant(gemm, fuse_y=False)
+    if acc is not None:
+        for fam, (slices, sep) in enumerate(acc):
+            g.set_tc_accum(gemm, fam, slices, sep)
+    for n in (50, 100):
+        g.step(50)
+        errs = rel_errors(g.get(ALL), ref[n], skip=("Ez", "uz"))
+        for k, v in errs.items():
+            assert v <= mixed_bar(k, n), (n, k, v)
+    g.close()
+
+
+def test_tc_accumulation_rejects():
+    wl = workloads.small3d(ex=2, ey=2, order=4, nz=4)
+    g = native.from_workload(wl, precision=native.PF_MIXED)
+    for args in [(1, 0, 1, 0), (native.PF_GEMM_TC, 2, 1, 0), (native.PF_GEMM_TC, 0, 0, 0),
+                 (native.PF_GEMM_TC, 1, 65, 0), (native.PF_GEMM_TC, 1, 2, 2)]:
+        with pytest.raises(RuntimeError):
+            g.set_tc_accum(*args)
+    g.close()
+    g64 = native.from_workload(wl, precision=native.PF_FP64)
+    with pytest.raises(RuntimeError):
+        g64.set_tc_accum(native.PF_GEMM_TC, 1, 2, 1)
+    g64.close()
