@@ -1022,7 +1022,8 @@ struct Engine {
                     pf::DTab<KC> t;
                     for (int i = 0; i < (KC + 1) * (KC + 1); ++i) t.d[i] = (float)hs.D[i];
                     for (int i = 0; i <= KC; ++i) t.w[i] = (float)hs.w[i];
-                    pf::k_efield_rows<KC><<<dim3(ey, nz), 256, rows_smem, st>>>(geo(), t, Vf, Ex, Ey);
+                    const unsigned thr = (unsigned)std::min(1024, (nx + 31) / 32 * 32);
+                    pf::k_efield_rows<KC><<<dim3(ey, nz), thr, rows_smem, st>>>(geo(), t, Vf, Ex, Ey);
                     return;
                 }
             }

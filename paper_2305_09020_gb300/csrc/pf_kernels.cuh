@@ -302,8 +302,9 @@ __global__ void k_efield(Geo<T> G_, const T *__restrict__ V, T *__restrict__ Ex,
 // column (y), so that the derivative weights are the same in every thread and come from the
 // kernel's parameters: K + 1 (2K + 2 at element boundaries) values per K nodes instead of up to
 // 4(K + 1) loads per node.  The node rows of the block are staged in shared memory; E_x goes
-// through shared memory so that its global stores coalesce.  Same sums in the same order as
-// k_efield.
+// through shared memory so that its global stores coalesce.  A block has one thread per node
+// column (n_x rounded up to a warp, at most 1024), so both passes take about one round.  Same
+// sums in the same order as k_efield.
 template <int KC>
 struct DTab {
     float d[(KC + 1) * (KC + 1)];   // D[a (K+1) + m]
@@ -311,7 +312,7 @@ struct DTab {
 };
 
 template <int KC>
-__global__ void __launch_bounds__(256) k_efield_rows(Geo<float> G_, DTab<KC> t, const float *__restrict__ V,
+__global__ void __launch_bounds__(1024) k_efield_rows(Geo<float> G_, DTab<KC> t, const float *__restrict__ V,
                                                      float *__restrict__ Ex, float *__restrict__ Ey) {
     constexpr int K = KC, P = KC + 1;
     const Geo<float> G = fixed_order<KC>(G_);

@@ -2,15 +2,18 @@
 // (the constant eigenbasis products of the Remark after Algorithm 2).
 //
 // C[M x N] = A[M x K] * B[K x N] in "3xTF32": A and B are split into TF32 heads and tails
-// (x = hi + lo, both rounded to nearest) and the tensor core accumulates hi*hi + hi*lo + lo*hi in
-// FP32; the dropped lo*lo term is ~2^-22 relative, so the product has single-precision accuracy.
-// B (an eigenbasis, constant for the run) is split once on the host and stored transposed and
-// zero padded as Bt[Npad][Kpad] (K-major); A is split in shared memory after it lands.
+// (x = hi + lo) and the tensor core accumulates hi*hi + hi*lo + lo*hi in FP32; the dropped lo*lo
+// term is ~2^-21 relative, so the product has single-precision accuracy.  B (an eigenbasis,
+// constant for the run) is split once on the host (both parts rounded to nearest) and stored
+// transposed and zero padded as Bt[Npad][Kpad] (K-major).  A's head is the landed FP32 chunk
+// itself, which the tensor core truncates to TF32; its tail, the exact remainder rounded to
+// nearest, is written to shared memory after the chunk lands.
 //
 // Persistent, warp-specialised kernel; one CTA per SM walks tiles of 128 rows x BN columns:
 //   warp 8      TMA producer: per 32-wide K chunk, A (128 x 32) and both halves of Bt (BN x 32)
 //               into a ring of shared-memory stages (128-byte swizzle, the layout the MMA reads)
-//   warps 10-11 split each landed A chunk into hi (in place) and lo (a second buffer)
+//   warps 10-11 write the TF32 tail of each landed A chunk into a second buffer (the landed chunk
+//               is the head: the tensor core truncates FP32 words to TF32)
 //   warp 9      one thread issues tcgen05.mma (M = 128, N = BN, K = 8) and commits to mbarriers
 //   warps 0-7   drain the TMEM accumulators into FP32 registers (all of a thread's columns loaded
 //               before one wait) and run the epilogue; setmaxnreg moves registers from warps 8-11
@@ -86,6 +89,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
+
+// the TF32 value the tensor core takes from an FP32 word: its upper 19 bits
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // K-major, 128-byte swizzle, 8-row atoms of 1024 bytes: matrix descriptor of a tile at addr
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
@@ -330,7 +336,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint64_t ds = dbase;
             bool ok = true;
             for (int q = 0; q < Q && ok; ++q) {
-                if (!mbar_wait(b_conv + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
+                // sep: the products with A's head start once the chunk has landed, the ones with its
+                // tail once the split warps have written it; otherwise every product waits for them
+                if (!mbar_wait((SEP ? b_full : b_conv) + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
                 // sep: the tile's correction region (it & 1) is free once its previous tile is drained
                 if (SEP && c == 0 &&
                     !mbar_wait(b_cempty + 8 * (it & 1), (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, g.wait_ns)) {
@@ -357,9 +365,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t d = tmem + rbase + (uint32_t)(r * BN);
                     const uint64_t o = ds + 2 * kk;     // this 8-wide K slice: 32 bytes further
-                    if (SEP) {   // correction products into the tile's region, the main one into the group's
-                        mma_tf32(dcor, o + daL, o + dbH, idesc, (c == 0 && kk == 0) ? 0u : 1u);
-                        mma_tf32(dcor, o, o + dbL, idesc, 1u);
+                    if (SEP) {   // head x tail of B into the tile's region, the main product into the group's
+                        mma_tf32(dcor, o, o + dbL, idesc, (c == 0 && kk == 0) ? 0u : 1u);
                         mma_tf32(d, o, o + dbH, idesc, first ? 0u : 1u);
                     } else {     // the two small correction products first, then the main term
                         mma_tf32(d, o + daL, o + dbH, idesc, first ? 0u : 1u);
@@ -375,9 +382,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                if (SEP && last_chunk) {
-                    mma_commit(b_cfull + 8 * (it & 1));
-                    ++it;
+                if (SEP) {   // A's tail x head of B, once the split warps are done with the chunk
+                    if (!mbar_wait(b_conv + 8 * s, ph, abort_flag, g.wait_ns)) { fail(); break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int kk = 0; kk < TC_KC / 8; ++kk) mma_tf32(dcor, ds + 2 * kk + daL, ds + 2 * kk + dbH, idesc, 1u);
+                    if (last_chunk) {
+                        mma_commit(b_cfull + 8 * (it & 1));
+                        ++it;
+                    }
                 }
                 mma_commit(b_empty + 8 * s);   // the stage is free once these MMAs have read it
                 if (++s == S) { s = 0; ph ^= 1u; ds = dbase; } else { ds += dstage; }
@@ -502,7 +515,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (!ok) fail();
     } else {
-        // ---- split A into TF32 head (in place) and tail (warps 10-11: 64 floats a thread) -----
+        // ---- A's TF32 tail (warps 10-11: 64 floats a thread) ---------------------------------
+        // The tensor core reads a TF32 operand by truncating the FP32 word to its upper 19 bits
+        // (measured on the GB300: 1 + 3 2^-12 enters an MMA as 1), so the landed A serves as the
+        // head as it is; the tail is the exact remainder x - trunc(x), rounded to nearest TF32.
         const int ct = tid - (TC_EPI_WARPS + 2) * 32;   // 0 .. 32 TC_CONV_WARPS - 1
         int s = 0;
         uint32_t ph = 0;
@@ -516,12 +532,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int i = ct; i < (int)(ABYTES / 16); i += 32 * TC_CONV_WARPS) {
                 const uint32_t off = (uint32_t)(16 * i);
                 const float4 x = *(const float4 *)(sa + off);
-                float4 h, l;
-                h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
-                h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
-                h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
-                h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
-                *(float4 *)(sa + off) = h;
+                float4 l;
+                l.x = tf32_rna(x.x - tf32_trunc(x.x));
+                l.y = tf32_rna(x.y - tf32_trunc(x.y));
+                l.z = tf32_rna(x.z - tf32_trunc(x.z));
+                l.w = tf32_rna(x.w - tf32_trunc(x.w));
                 *(float4 *)(sa + ABYTES + off) = l;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
