@@ -689,13 +689,15 @@ struct Engine {
     }
     // transform buffers of a non-power-of-two nz need a second (scratch) copy for the mixed radices
     bool nz_pow2() const { return (nz & (nz - 1)) == 0; }
+    // row pitch of a pencil in the z-transform buffers (the kernels' pf::fft_ld)
+    int fld() const { return (sizeof(T) == 4 && lgz() == 8) ? 289 : nz + 1; }
     size_t fft_scratch(int pencils) const { return nz_pow2() ? 0 : (size_t)pencils * (nz + 1) * sizeof(cplx<T>); }
     // shared memory of the z-transform pencils: 72 KB for 2^k planes (the FFT itself runs in
     // registers for FP32 32..256 planes), half of it for the mixed radices (a scratch copy)
     static constexpr int FFT_SMEM_BUDGET = 73728;
     static constexpr size_t FFT_SMEM_LIMIT = 96 * 1024;   // raised once per kernel at set-up
     int fwd_tp() const {
-        int tp = (int)((nz_pow2() ? FFT_SMEM_BUDGET : FFT_SMEM_BUDGET / 2) / (sizeof(cplx<T>) * (nz + 1)));
+        int tp = (int)((nz_pow2() ? FFT_SMEM_BUDGET : FFT_SMEM_BUDGET / 2) / (sizeof(cplx<T>) * fld()));
         const int by_grid = tp_override > 0 ? tp_override : n2 / (4 * 152);
         if (tp > by_grid) tp = by_grid;
         if (tp > 64) tp = 64;
@@ -900,7 +902,7 @@ struct Engine {
         a.X0 = X0; a.x0_local = x0l; a.X1 = X1; a.x1_local = x1l; a.mult = mult; a.scale = (T)scale;
         a.lift = lift; a.out = out; a.out1 = out1; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int) +
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * fld()) * sizeof(cplx<T>) + a.tp * 4 * sizeof(int) +
                             fft_scratch(a.tp);
         prof->begin(PF_KC_FWD, st);
         const dim3 grid((n2 + a.tp - 1) / a.tp, ncomp);
@@ -922,7 +924,7 @@ struct Engine {
         a.Y = Y; a.phi_variant = 0; a.drow0 = drow0; a.drow1 = drow1; a.v0 = (T)v0; a.v1 = (T)v1;
         a.out = out; a.dzout = d3 ? dzout : nullptr; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz);
         a.tw = tw; a.tp = fwd_tp();
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(a.tp);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + a.tp * fld()) * sizeof(cplx<T>) + fft_scratch(a.tp);
         prof->begin(PF_KC_INV, st);
         launch_inv(dim3((n2 + a.tp - 1) / a.tp, ncomp), smem, a);
         check_launch();
@@ -936,7 +938,7 @@ struct Engine {
         a.out = phi_out; a.dzout = d3 ? dzphi_out : nullptr; a.out2 = W; a.dzout2 = d3 ? dzW : nullptr;
         a.out3 = Lf; a.two_pi_over_lz = (T)(2.0 * M_PI / hs.lz); a.tw = tw;
         a.tp = std::max(4, fwd_tp() / 2);    // still a power of two
-        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * (nz + 1)) * sizeof(cplx<T>) + fft_scratch(2 * a.tp);
+        const size_t smem = (size_t)((nz > 1 ? nz / 2 : 1) + 2 * a.tp * fld()) * sizeof(cplx<T>) + fft_scratch(2 * a.tp);
         prof->begin(PF_KC_INV, st);
         launch_inv(dim3((n2 + a.tp - 1) / a.tp), smem, a);
         check_launch();

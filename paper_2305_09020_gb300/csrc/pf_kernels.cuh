@@ -721,6 +721,106 @@ __device__ __forceinline__ void fft_pencils_warp(cplx<T> *buf, int ld, int npen,
     __syncthreads();
 }
 
+// 8-point DFT of v in registers, natural order in and out (radix-2 decimation in frequency,
+// the bit-reversed result renamed at compile time); w8 = exp(-+ i pi / 4)
+template <typename T>
+__device__ __forceinline__ void dft8(cplx<T> *v, bool inverse) {
+    const T r = T(0.70710678118654752440);
+    const T sg = inverse ? T(1) : T(-1);   // sign of the imaginary part of w8
+    cplx<T> a[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {          // span 4, twiddles w8^j
+        const cplx<T> p = v[j], q = v[j + 4];
+        a[j] = {p.x + q.x, p.y + q.y};
+        const cplx<T> d = {p.x - q.x, p.y - q.y};
+        if (j == 0) a[4] = d;
+        else if (j == 1) a[5] = {r * (d.x - sg * d.y), r * (d.y + sg * d.x)};
+        else if (j == 2) a[6] = {-sg * d.y, sg * d.x};
+        else a[7] = {r * (-d.x - sg * d.y), r * (-d.y + sg * d.x)};
+    }
+#pragma unroll
+    for (int h = 0; h < 8; h += 4) {       // span 2, twiddles w8^(2j) = 1, -+i
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const cplx<T> p = a[h + j], q = a[h + j + 2];
+            a[h + j] = {p.x + q.x, p.y + q.y};
+            const cplx<T> d = {p.x - q.x, p.y - q.y};
+            a[h + j + 2] = j == 0 ? d : cplx<T>{-sg * d.y, sg * d.x};
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 8; h += 2) {       // span 1
+        const cplx<T> p = a[h], q = a[h + 1];
+        a[h] = {p.x + q.x, p.y + q.y};
+        a[h + 1] = {p.x - q.x, p.y - q.y};
+    }
+    // a[i] holds output bitrev3(i)
+    v[0] = a[0]; v[4] = a[1]; v[2] = a[2]; v[6] = a[3]; v[1] = a[4]; v[5] = a[5]; v[3] = a[6]; v[7] = a[7];
+}
+
+// w^m, w = exp(-+ 2 pi i / 256), 0 <= m < 256, from the half table tw (w^(m + 128) = -w^m)
+template <typename T>
+__device__ __forceinline__ cplx<T> tw256(const cplx<T> *tw, int m, bool inverse) {
+    cplx<T> w = tw[m & 127];
+    if (m & 128) w = {-w.x, -w.y};
+    if (inverse) w.y = -w.y;
+    return w;
+}
+
+// 256-point FFT of npen pencils, one warp per pencil, natural order in and out, in four steps
+// (256 = 8 x 32 = 8 x 8 x 4): lane l takes x[l + 32 e] (e < 8) and runs an 8-point DFT over e,
+// twiddled by w^(l k1); a transpose through the pencil's own buffer (rows of 36 so that the reads
+// below hit every bank pair twice) gives lane (k1, l1) = 4 k1 + l1 the eight values of lanes
+// l1 + 4 l2, an 8-point DFT over l2 twiddled by w32^(l1 k2); a 4-point DFT over l1 across the four
+// lanes of a quad (two shuffle stages) completes X[k1 + 8 k2 + 64 k3].  The pencil buffer must
+// hold 8 x 36 = 288 values (ld >= 288).  Called after the block barrier that completes the
+// loads; ends with a block barrier.
+template <typename T>
+__device__ __forceinline__ void fft256_warp(cplx<T> *buf, int ld, int npen, const cplx<T> *tw, bool inverse) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int k1q = lane >> 2, l1 = lane & 3;
+    for (int pen = warp; pen < npen; pen += nwarp) {
+        cplx<T> *x = buf + pen * ld;
+        cplx<T> v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = x[lane + 32 * e];
+        dft8(v, inverse);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], tw256(tw, lane * k, inverse));
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k * 36 + lane] = v[k];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = x[k1q * 36 + 4 * j + l1];
+        dft8(v, inverse);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], tw256(tw, 8 * l1 * k, inverse));
+        // 4-point DFT over l1 (the quad's lanes): pairs l1, l1 ^ 2, then l1, l1 ^ 1; lane l1 ends
+        // with output k3 = {0, 2, 1, 3}[l1]
+        const T sg = inverse ? T(1) : T(-1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cplx<T> p;
+            p.x = __shfl_xor_sync(0xffffffffu, v[k].x, 2);
+            p.y = __shfl_xor_sync(0xffffffffu, v[k].y, 2);
+            v[k] = l1 < 2 ? cplx<T>{v[k].x + p.x, v[k].y + p.y} : cplx<T>{p.x - v[k].x, p.y - v[k].y};
+            p.x = __shfl_xor_sync(0xffffffffu, v[k].x, 1);
+            p.y = __shfl_xor_sync(0xffffffffu, v[k].y, 1);
+            if (l1 == 0) v[k] = {v[k].x + p.x, v[k].y + p.y};
+            else if (l1 == 1) v[k] = {p.x - v[k].x, p.y - v[k].y};
+            else if (l1 == 2) v[k] = {v[k].x - sg * p.y, v[k].y + sg * p.x};   // + w4 p, w4 = -+i
+            else v[k] = {p.x + sg * v[k].y, p.y - sg * v[k].x};                 // p - w4 v
+        }
+        const int k3 = (l1 == 1) ? 2 : (l1 == 2) ? 1 : l1;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k1q + 8 * k + 64 * k3] = v[k];
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
 // Stockham autosort FFT of npen pencils of any even length n = 2^a 3^b 5^c 7^d (natural order in
 // and out; the result ends in buf, tmp is scratch of the same shape).  Each stage of radix R
 // (4, 2, 3, 5 or 7, taken in that order while it divides what is left) combines R inputs
@@ -782,6 +882,13 @@ __device__ void fft_pencils_mixed(cplx<T> *buf, cplx<T> *tmp, int ld, int npen, 
         __syncthreads();
     }
 }
+
+// FP32 256-plane transforms run fft256_warp: natural order and 289-value pencil rows (it
+// transposes through the pencil's own buffer); every other transform: bit-reversed DIT, nz + 1
+template <typename T, int LGZ>
+__host__ __device__ constexpr bool fft_four_step() { return LGZ == 8 && sizeof(T) == 4; }
+template <typename T, int LGZ>
+__host__ __device__ constexpr int fft_ld(int nz) { return fft_four_step<T, LGZ>() ? 289 : nz + 1; }
 
 // position of sample (or mode) i in the transform buffer: bit-reversed for the radix-2 DIT
 __device__ __forceinline__ int fft_slot(int i, int bits, bool pow2) { return pow2 ? bitrev(i, bits) : i; }
@@ -853,10 +960,10 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
     }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
-    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = nz + 1, tp = a.tp;
+    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = fft_ld<T, LGZ>(nz), tp = a.tp;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
     int *ssrc = reinterpret_cast<int *>(buf + tp * ld);   // tp x 4 DSSUM sources
-    const bool pow2 = (nz & (nz - 1)) == 0;
+    const bool pow2 = (nz & (nz - 1)) == 0 && !fft_four_step<T, LGZ>();   // bit-reversed slots
     cplx<T> *tmp = reinterpret_cast<cplx<T> *>(ssrc + tp * 4);   // mixed-radix scratch (nz not 2^k)
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
@@ -898,7 +1005,9 @@ __global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
         }
     }
     __syncthreads();
-    if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+    if constexpr (fft_four_step<T, LGZ>()) {
+        fft256_warp(buf, ld, tp, stw, false);
+    } else if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
         fft_pencils_warp<T, LGZ>(buf, ld, tp, stw, false);
     } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp, nz, stw, false);
@@ -982,10 +1091,10 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
     }
     extern __shared__ unsigned char pf_smem_raw[];
     cplx<T> *stw = reinterpret_cast<cplx<T> *>(pf_smem_raw);
-    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = nz + 1, tp = a.tp;
+    const int nz = LGZ ? (1 << LGZ) : G.nz, ld = fft_ld<T, LGZ>(nz), tp = a.tp;
     const int npair = a.phi_variant ? 2 : 1;
     cplx<T> *buf = stw + (nz > 1 ? nz / 2 : 1);
-    const bool pow2 = (nz & (nz - 1)) == 0;
+    const bool pow2 = (nz & (nz - 1)) == 0 && !fft_four_step<T, LGZ>();   // bit-reversed slots
     cplx<T> *tmp = buf + tp * npair * ld;   // mixed-radix scratch (nz not 2^k)
     const int bits = 31 - __clz(nz);
     for (int i = threadIdx.x; i < nz / 2; i += blockDim.x) stw[i] = a.tw[i];
@@ -1041,7 +1150,9 @@ __global__ void k_inv(Geo<T> G, InvArgs<T> a) {
         }
     }
     __syncthreads();
-    if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
+    if constexpr (fft_four_step<T, LGZ>()) {
+        fft256_warp(buf, ld, tp * npair, stw, true);
+    } else if constexpr (LGZ >= 5 && sizeof(T) == 4) {   // FP64 keeps the shared-memory stages
         fft_pencils_warp<T, LGZ>(buf, ld, tp * npair, stw, true);
     } else if (nz > 1) {
         if (pow2) fft_pencils(buf, ld, tp * npair, nz, stw, true);
