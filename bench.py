@@ -170,7 +170,7 @@ def transform_kernel(code, fused_y):
 
 # DRAM traffic per launch of a transform kernel, from one ncu capture of an unchanged kernel
 # (profiles/): (workload, precision, variant code, fused y) -> bytes
-TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("droplet3d", "mixed", 3, 0): 2.24e6}
+TRANSFORM_DRAM_BYTES_PER_LAUNCH = {("droplet3d", "mixed", 3, 0): 2.24e6, ("layers3d", "mixed", 0, 0): 5.49e7}
 
 
 def transform_bytes_per_launch(nx, ny, nz, prec):
@@ -508,7 +508,8 @@ def main():
                          "traffic": traffic,
                          "traffic_note": None if traffic is None else
                          "DRAM bytes per transform launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                         "mean over one solve's launches on this workload, profiles/); algorithmic "
+                         "mean over one solve's launches on this workload, profiles/; layers3d captured with "
+                         "128 planes and scaled to 256 by the rows processed); algorithmic "
                          f"{transform_bytes_per_launch(nx, ny, nz, prec):.3e} B per launch"})
         else:
             roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",

@@ -382,8 +382,12 @@ void pf_batch_destroy(pf_batch *b);
  * on [x0, x1) with cells starting at x0 + i (x1-x0)/gnx, y from y0 to y1 inclusive), which a
  * fixed bilinear map carries to the nqx x nqy nodes (node_x[nqx], node_y[nqy]; [y][x] order).
  * Weights are BF16 in the products (FP32 master copies), activations and sums FP32; Glorot
- * initialisation from seed.  All work runs on cuda_stream.  Errors: PF_EINVAL, PF_ENOMEM,
- * PF_ECUDA (messages in pf_last_error(NULL)). */
+ * initialisation from seed.  The forward products of hidden and output layers whose input width
+ * is a multiple of 64 up to 384 and whose output width is a multiple of 128 run on the tensor
+ * cores (tcgen05.mma kind::f16: the BF16 weights times the inputs split into BF16 head and tail,
+ * FP32 accumulation); the first layer and the backward products run on the CUDA cores.  All work
+ * runs on cuda_stream.  Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT when a tensor-core
+ * layer's bounded wait gave up (messages in pf_last_error(NULL)). */
 typedef struct pf_no pf_no;
 int pf_no_create(int nlayer, const int *dims, const double *feat_mean, const double *feat_std, int gnx, int gny,
                  double x0, double x1, double y0, double y1, int nqx, int nqy, const double *node_x,

@@ -23,6 +23,8 @@
 #include <vector>
 
 #include "../../include/pf.h"
+#define PF_TC_HELPERS_ONLY
+#include "pf_tc.cuh"
 
 void pf_internal_set_error(const std::string &msg);
 
@@ -51,6 +53,118 @@ __global__ void k_dense_fwd(const float *__restrict__ X, const __nv_bfloat16 *__
         s += x * __bfloat162float(W[(long long)k * N + n]);
     }
     Y[(long long)r * N + n] = tanhf(s);
+}
+
+// The same dense layer on the tensor cores, for hidden and output layers with K % 64 == 0,
+// K <= 384 and N % 128 == 0: one CTA per 128 outputs x 64 samples.  A = the layer's BF16 weights,
+// transposed (Wt[N][K], K-major), B = the FP32 inputs split into BF16 head and tail (x = hi + lo,
+// both rounded to nearest: the inputs keep ~16 bits, the weights are BF16 anyway);
+// tcgen05.mma kind::f16 (M = 128, N = 64, K = 16) accumulates Wt (hi + lo) in FP32 in tensor memory,
+// the epilogue adds the bias and applies tanh.  Operands are staged by the block's threads in the
+// 128-byte-swizzled K-major layout (K in atoms of 64 BF16; rows of 128 bytes, 16-byte chunks
+// permuted by row mod 8).  The one wait is bounded: on time-out the error word is set.
+constexpr int NO_TC_BN = 64;   // samples per CTA
+__device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
+    // byte offset of BF16 element (row, k) in a K-major, 128B-swizzled tile of `rows` rows
+    const int atom = k >> 6, c = (k & 63) * 2;
+    return (uint32_t)(atom * rows * 128 + row * 128 + ((((c >> 4) ^ (row & 7))) << 4) + (c & 15));
+}
+__global__ void __launch_bounds__(128, 1) k_dense_fwd_tc(const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Wt,
+                                                         const float *__restrict__ b, float *__restrict__ Y, int B, int K,
+                                                         int N, int *err) {
+    extern __shared__ __align__(1024) unsigned char no_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)no_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;                                   // 128 x K
+    unsigned char *sBh = sA + 128 * K * 2, *sBl = sBh + NO_TC_BN * K * 2;   // 64 x K each
+    uint64_t *mbar = (uint64_t *)(sBl + NO_TC_BN * K * 2);
+    uint32_t *slot = (uint32_t *)(mbar + 1);
+    const int n0 = blockIdx.x * 128, r0 = blockIdx.y * NO_TC_BN, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights: 16-byte chunks of Wt rows
+    const int cpr = K / 8;   // chunks per row
+    for (int i = tid; i < 128 * cpr; i += blockDim.x) {
+        const int row = i / cpr, kc = (i - row * cpr) * 8;
+        const uint4 v = *reinterpret_cast<const uint4 *>(Wt + (size_t)(n0 + row) * K + kc);
+        *reinterpret_cast<uint4 *>(sA + sw128_off(row, kc, 128)) = v;
+    }
+    // inputs: head and tail in BF16 (rows past B are zero)
+    for (int i = tid; i < NO_TC_BN * (K / 2); i += blockDim.x) {
+        const int row = i / (K / 2), k = (i - row * (K / 2)) * 2;
+        float2 x = make_float2(0.f, 0.f);
+        if (r0 + row < B) x = *reinterpret_cast<const float2 *>(X + (size_t)(r0 + row) * K + k);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+        *reinterpret_cast<__nv_bfloat162 *>(sBh + sw128_off(row, k, NO_TC_BN)) = h;
+        *reinterpret_cast<__nv_bfloat162 *>(sBl + sw128_off(row, k, NO_TC_BN)) = l;
+    }
+    if (tid == 0) {
+        pf::mbar_init(pf::smem_u32(mbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(pf::smem_u32(slot)),
+                     "r"(NO_TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot;
+    if (tid == 0) {
+        // instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 64
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NO_TC_BN >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+        const uint32_t a0 = pf::smem_u32(sA), bh0 = pf::smem_u32(sBh), bl0 = pf::smem_u32(sBl);
+        for (int s = 0; s < K / 16; ++s) {   // 16 BF16 = 32 bytes per K step
+            const uint32_t oa = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
+            const uint32_t ob = (uint32_t)((s >> 2) * NO_TC_BN * 128 + (s & 3) * 32);
+            const uint64_t da = pf::sdesc_sw128(a0 + oa);
+            uint32_t acc = s > 0 ? 1u : 0u;
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                         "l"(da), "l"(pf::sdesc_sw128(bh0 + ob)), "r"(idesc), "r"(acc));
+            acc = 1u;
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                         "l"(da), "l"(pf::sdesc_sw128(bl0 + ob)), "r"(idesc), "r"(acc));
+        }
+        pf::mma_commit(pf::smem_u32(mbar));
+    }
+    const bool ok = pf::mbar_wait(pf::smem_u32(mbar), 0u, nullptr, 1000000000ull);
+    if (!ok && lane == 0) atomicExch(err, pf::TC_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // warp w reads rows (outputs) 32 w .. 32 w + 31, all 64 samples
+        float v[64];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        pf::tmem_ld32(ta, v);
+        pf::tmem_ld32(ta + 32, v + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int n = n0 + warp * 32 + lane;
+        const float bn = b[n];
+#pragma unroll
+        for (int c = 0; c < NO_TC_BN; ++c)
+            if (r0 + c < B) Y[(size_t)(r0 + c) * N + n] = tanhf(v[c] + bn);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NO_TC_BN) : "memory");
+    }
+}
+
+// Wt[n][k] = W[k][n] (BF16) for the tensor-core layers
+__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ W, __nv_bfloat16 *__restrict__ Wt, int K, int N) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y)
+        if (k0 + i < K && n0 + threadIdx.x < N) t[i][threadIdx.x] = W[(size_t)(k0 + i) * N + n0 + threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y)
+        if (n0 + i < N && k0 + threadIdx.x < K) Wt[(size_t)(n0 + i) * K + k0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
 // dZ = dY (1 - Y^2) in place on dY
@@ -200,6 +314,8 @@ struct pf_no {
     long long nparam = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb = nullptr;
+    std::vector<__nv_bfloat16 *> wt;       // per layer: BF16 weights transposed for the tensor cores (or null)
+    int *err = nullptr;                    // device error word of the tensor-core layers (bounded waits)
     float *mean = nullptr, *istd = nullptr;
     int *ridx = nullptr, *rp = nullptr, *rc = nullptr;
     float *rw = nullptr, *rv = nullptr;
@@ -241,11 +357,36 @@ void ensure_batch(pf_no *h, int B) {
     h->maxB = B;
 }
 
+// layers on the tensor cores: hidden and output layers with K a multiple of 64 up to 384 and N a
+// multiple of 128 (the first layer standardises its 3 inputs on the CUDA cores)
+bool tc_layer(const pf_no *h, int l) {
+    const int K = h->dims[l], N = h->dims[l + 1];
+    return l > 0 && K % 64 == 0 && K <= 384 && N % 128 == 0;
+}
+size_t tc_smem(int K) { return 1024 + (size_t)128 * K * 2 + (size_t)2 * NO_TC_BN * K * 2 + 64; }
+
+// the transposed BF16 copies of the tensor-core layers' weights, after every change of wb
+void refresh_wt(pf_no *h) {
+    for (int l = 0; l + 1 < (int)h->dims.size(); ++l)
+        if (h->wt[l]) {
+            const int K = h->dims[l], N = h->dims[l + 1];
+            k_transpose_bf16<<<dim3((N + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, h->st>>>(h->wb + h->woff[l], h->wt[l],
+                                                                                           K, N);
+            NO_CU(cudaGetLastError());
+        }
+}
+
 // forward from h->act[0] (B x 3 raw features) to h->pn (B x nq)
 void forward(pf_no *h, int B) {
     const int L = (int)h->dims.size() - 1;
     for (int l = 0; l < L; ++l) {
         const int K = h->dims[l], N = h->dims[l + 1];
+        if (h->wt[l]) {
+            k_dense_fwd_tc<<<dim3(N / 128, (B + NO_TC_BN - 1) / NO_TC_BN), 128, tc_smem(K), h->st>>>(
+                h->act[l], h->wt[l], h->w + h->boff[l], h->act[l + 1], B, K, N, h->err);
+            NO_CU(cudaGetLastError());
+            continue;
+        }
         dim3 grid((N + 127) / 128, B);
         k_dense_fwd<<<grid, 128, 0, h->st>>>(h->act[l], h->wb + h->woff[l], h->w + h->boff[l], h->act[l + 1], B, K, N,
                                              l == 0 ? h->mean : nullptr, l == 0 ? h->istd : nullptr);
@@ -296,11 +437,25 @@ void adam(pf_no *h, double lr) {
     k_adam<<<(unsigned)((h->nparam + 255) / 256), 256, 0, h->st>>>(h->w, h->wb, h->g, h->m, h->v, h->nparam, (float)lr,
                                                                    b1, b2, c1, c2, 1e-8f);
     NO_CU(cudaGetLastError());
+    refresh_wt(h);
 }
 
 int no_fail(int code, const std::string &m) {
     pf_internal_set_error(m);
     return code;
+}
+
+// the tensor-core layers' error word after a synchronised call: PF_ETIMEOUT (and cleared) when a
+// bounded wait gave up
+int tc_status(pf_no *h) {
+    int e = 0;
+    if (cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return no_fail(PF_ECUDA, "pf_no: reading the error word");
+    }
+    if (e == 0) return PF_OK;
+    cudaMemset(h->err, 0, sizeof(int));
+    return no_fail(PF_ETIMEOUT, "pf_no: a tensor-core layer's bounded wait gave up");
 }
 
 void upload_features(pf_no *h, int B, const double *feat) {
@@ -355,6 +510,19 @@ extern "C" int pf_no_create(int nlayer, const int *dims, const double *feat_mean
         NO_CU(cudaMemcpy(h->w, w.data(), off * 4, cudaMemcpyHostToDevice));
         k_to_bf16<<<(unsigned)((off + 255) / 256), 256>>>(h->w, h->wb, off);
         NO_CU(cudaGetLastError());
+        NO_CU(cudaDeviceSynchronize());
+        h->err = h->mk<int>(1);
+        h->wt.assign(nlayer - 1, nullptr);
+        int kmax = 0;
+        for (int l = 0; l + 1 < nlayer; ++l)
+            if (tc_layer(h.get(), l)) {
+                h->wt[l] = h->mk<__nv_bfloat16>((size_t)dims[l] * dims[l + 1]);
+                kmax = std::max(kmax, dims[l]);
+            }
+        if (kmax > 0)
+            NO_CU(cudaFuncSetAttribute(k_dense_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(kmax)));
+        refresh_wt(h.get());
+        NO_CU(cudaStreamSynchronize(h->st));
         std::vector<float> mu(dims[0]), is(dims[0]);
         for (int k = 0; k < dims[0]; ++k) {
             mu[k] = (float)feat_mean[k];
@@ -445,6 +613,8 @@ extern "C" int pf_no_set_params(pf_no *h, const double *host, size_t n) {
         NO_CU(cudaMemcpyAsync(h->w, w.data(), h->nparam * 4, cudaMemcpyHostToDevice, h->st));
         k_to_bf16<<<(unsigned)((h->nparam + 255) / 256), 256, 0, h->st>>>(h->w, h->wb, h->nparam);
         NO_CU(cudaGetLastError());
+        refresh_wt(h);
+        NO_CU(cudaGetLastError());
         NO_CU(cudaStreamSynchronize(h->st));
     } catch (const NoErr &e) {
         return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
@@ -465,7 +635,7 @@ extern "C" int pf_no_predict(pf_no *h, int B, const double *feat, double *phi_no
     } catch (const NoErr &e) {
         return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
     }
-    return PF_OK;
+    return tc_status(h);
 }
 
 extern "C" int pf_no_predict_mass(pf_no *h, int B, const double *feat, const double *mass, const double *wx,
@@ -492,7 +662,7 @@ extern "C" int pf_no_predict_mass(pf_no *h, int B, const double *feat, const dou
     } catch (const NoErr &e) {
         return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
     }
-    return PF_OK;
+    return tc_status(h);
 }
 
 extern "C" int pf_no_loss_grad(pf_no *h, int B, const double *feat, const double *target, double *loss,
@@ -515,7 +685,7 @@ extern "C" int pf_no_loss_grad(pf_no *h, int B, const double *feat, const double
     } catch (const NoErr &e) {
         return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
     }
-    return PF_OK;
+    return tc_status(h);
 }
 
 extern "C" int pf_no_train(pf_no *h, int nsample, const double *feat, const double *target, int batch, int epochs,
@@ -559,7 +729,7 @@ extern "C" int pf_no_train(pf_no *h, int nsample, const double *feat, const doub
     } catch (const NoErr &e) {
         return no_fail(PF_ECUDA, e.where + ": " + cudaGetErrorString(e.code));
     }
-    return PF_OK;
+    return tc_status(h);
 }
 
 extern "C" void pf_no_destroy(pf_no *h) {

@@ -24,7 +24,9 @@ def test_transform_kernel_labels_and_traffic_table():
     assert bench.transform_kernel(6, 1) == "k_fdm_cluster<4>"
     assert bench.transform_kernel(8, 1) == "k_gemm_tc + k_gemm_cp"
     # only captured (precision, variant, fused y) triples carry a DRAM traffic figure
-    assert set(bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH) == {("droplet3d", "mixed", 3, 0)}
+    assert set(bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH) == {("droplet3d", "mixed", 3, 0), ("layers3d", "mixed", 0, 0)}
+    # the layers3d figure is at least the planes read once (13.19M FP32 values) and at most twice that
+    assert 4 * 13189120 <= bench.TRANSFORM_DRAM_BYTES_PER_LAUNCH[("layers3d", "mixed", 0, 0)] <= 8 * 13189120
     assert bench.transform_bytes_per_launch(128, 65, 64, 1) == pytest.approx(4 * (2 * 128 * 65 * 64 + 128 ** 2))
 
 

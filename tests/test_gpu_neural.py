@@ -33,6 +33,28 @@ def test_gradients_match_fp64_reference():
     no.close()
 
 
+def test_tensor_core_layers_match_fp64_reference():
+    """Layer widths that run the hidden and output layers on the tensor cores (K = 64, 128, N = 128,
+    256: tcgen05 kind::f16, BF16 weights, inputs split into BF16 head and tail, FP32 accumulation)
+    and a batch of 80 (two 64-sample column blocks), against the FP64 reference: the inputs keep
+    ~16 bits, so the predictions agree to 2e-5 and the gradients (CUDA-core backward) to 1e-4."""
+    rng = np.random.default_rng(11)
+    dims = [3, 64, 128, 16 * 16]
+    node_x = np.sort(rng.uniform(0.0, 2.0, 13))
+    node_y = np.linspace(0.0, 1.0, 7)
+    mean, std = np.array([1.5, 8.0, 0.1]), np.array([0.8, 5.0, 0.05])
+    no = native.NeuralOperator(dims, mean, std, (16, 16), (0.0, 2.0, 0.0, 1.0), node_x, node_y, seed=11)
+    R = bilinear_map(16, 16, (0.0, 2.0, 0.0, 1.0), node_x, node_y)
+    feat = np.column_stack([rng.uniform(0, 3, 80), rng.uniform(2, 20, 80), rng.uniform(0.03, 0.2, 80)])
+    tgt = np.tanh(rng.standard_normal((80, R.shape[0])))
+    loss, g = no.loss_grad(feat, tgt)
+    lref, gref, pred = loss_and_grad(no.params(), dims, mean, std, R, feat, tgt, bf16=True)
+    np.testing.assert_allclose(no.predict(feat), pred, atol=2e-5)
+    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    no.close()
+
+
 def test_training_reduces_loss():
     no, dims, mean, std, R, rng = small_operator(seed=5)
     feat = np.column_stack([rng.uniform(0, 3, 64), rng.uniform(2, 20, 64), rng.uniform(0.03, 0.2, 64)])
