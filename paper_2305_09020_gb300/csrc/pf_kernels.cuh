@@ -952,7 +952,7 @@ __device__ __forceinline__ T gather4(const T *__restrict__ L, long long zoff, co
 // LGZ > 0: Nz = 2^LGZ fixed at compile time (the FFT stages unroll, index arithmetic on Nz folds);
 // LGZ = 0: Nz from G (any supported value)
 template <typename T, int LGZ = 0>
-__global__ void k_fwd(Geo<T> G, FwdArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2) k_fwd(Geo<T> G, FwdArgs<T> a) {
     if (blockIdx.y) {   // component blockIdx.y of a batched launch
         a.X0 += blockIdx.y * a.cs_x0;
         if (a.X1) a.X1 += blockIdx.y * a.cs_x1;
