@@ -72,3 +72,61 @@ def test_fullsize_mixed_within_bars_of_fp64(fp64_run, gemm):
         assert np.linalg.norm(f32[k] - f64[k]) <= 5e-5 * np.linalg.norm(f64[k]), k
     for k in ("Ex", "Ey", "Ez", "P", "ux", "uy", "uz"):
         assert np.linalg.norm(f32[k] - f64[k]) <= 5e-4 * np.linalg.norm(f64[k]), k
+
+
+# ---- layers3d: the 3D benchmark workload (32x16 elements of order 10 x Nz = 256) ---------------
+@pytest.fixture(scope="module")
+def layers_fp64():
+    wl = workloads.layers3d()
+    h = native.from_workload(wl, precision=native.PF_FP64)
+    m0 = h.diagnostics()[0]
+    h.step(1)
+    m1 = h.diagnostics()[0]
+    h.step(4)
+    f = h.get(ALL)
+    h.close()
+    return wl, m0, m1, f
+
+
+def test_layers3d_mass_conserved_from_rest(layers_fp64):
+    _, m0, m1, _ = layers_fp64
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+
+
+def test_layers3d_mirror_symmetry(layers_fp64):
+    """Two flat layers and a drop centred at x = 1, z = 0.5: symmetric under x -> 2 - x and
+    z -> 1 - z (u_x and u_z antisymmetric under their own mirror).  Bar 1e-10 of each field's
+    maximum: at permittivity ratio 20 the initial potential's fixed point contracts by 19/20 per
+    iteration and stops at the FP64 stagnation point, ~20 x the last update away from the fixed
+    point, so mirror nodes start ~1e-11 apart (measured 2.2e-11 of max|V|)."""
+    _, _, _, f = layers_fp64
+    scale = {k: max(np.max(np.abs(v)), 1e-300) for k, v in f.items()}
+    for k in ("V", "phi", "P", "uy", "Ey"):
+        assert np.max(np.abs(f[k] - mirror_z(f[k]))) <= 1e-10 * scale[k], k
+        assert np.max(np.abs(f[k] - mirror_x(f[k]))) <= 1e-10 * scale[k], k
+    assert np.max(np.abs(f["uz"] + mirror_z(f["uz"]))) <= 1e-10 * scale["uz"]
+    assert np.max(np.abs(f["ux"] + mirror_x(f["ux"]))) <= 1e-10 * scale["ux"]
+
+
+def test_layers3d_mixed_within_bars_of_fp64(layers_fp64):
+    """The mixed path with its default transforms after five steps, against the FP64 path (itself
+    held to 1e-11 of the oracle on small meshes): V, phi, psi within 5e-5; the vector fields E and
+    u and the pressure within 5e-4.  E and u are compared as vectors: over flat layers E_x and u_x
+    come from the drop alone and are small beside E_y and u_y, so their own relative error is
+    not a measure of the field's."""
+    wl, _, _, f64 = layers_fp64
+    h = native.from_workload(wl, precision=native.PF_MIXED)
+    h.step(5)
+    f32 = h.get(ALL)
+    h.close()
+
+    def rel(keys):
+        num = sum(np.linalg.norm(f32[k] - f64[k]) ** 2 for k in keys)
+        den = sum(np.linalg.norm(f64[k]) ** 2 for k in keys)
+        return np.sqrt(num / den)
+
+    for k in ("V", "phi", "psi"):
+        assert rel((k,)) <= 5e-5, k
+    assert rel(("P",)) <= 5e-4
+    assert rel(("Ex", "Ey", "Ez")) <= 5e-4
+    assert rel(("ux", "uy", "uz")) <= 5e-4
