@@ -184,6 +184,67 @@ __device__ __forceinline__ T wdy(const T *F, const T *sDw, const T *sw, int p, i
     return s * hx2 * sw[a];
 }
 
+// The same derivatives of NF element arrays at once: each coefficient is loaded from shared
+// memory once for all NF fields (the sums per field are those of ddx/ddy/wdx/wdy, term by term)
+template <int NF, typename T>
+__device__ __forceinline__ void ddx_n(const T *const (&f)[NF], const T *sD, int p, int a, int b, T sc, T (&out)[NF]) {
+    T s[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s[i] = 0;
+#pragma unroll
+    for (int m = 0; m < p; ++m) {
+        const T d = sD[a * p + m];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) s[i] += d * f[i][b * p + m];
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) out[i] = s[i] * sc;
+}
+template <int NF, typename T>
+__device__ __forceinline__ void ddy_n(const T *const (&f)[NF], const T *sD, int p, int a, int b, T sc, T (&out)[NF]) {
+    T s[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s[i] = 0;
+#pragma unroll
+    for (int m = 0; m < p; ++m) {
+        const T d = sD[b * p + m];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) s[i] += d * f[i][m * p + a];
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) out[i] = s[i] * sc;
+}
+template <int NF, typename T>
+__device__ __forceinline__ void wdx_n(const T *const (&F)[NF], const T *sDw, const T *sw, int p, int a, int b, T hy2,
+                                      T (&out)[NF]) {
+    T s[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s[i] = 0;
+#pragma unroll
+    for (int m = 0; m < p; ++m) {
+        const T d = sDw[m * p + a];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) s[i] += d * F[i][b * p + m];
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) out[i] = s[i] * hy2 * sw[b];
+}
+template <int NF, typename T>
+__device__ __forceinline__ void wdy_n(const T *const (&F)[NF], const T *sDw, const T *sw, int p, int a, int b, T hx2,
+                                      T (&out)[NF]) {
+    T s[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s[i] = 0;
+#pragma unroll
+    for (int m = 0; m < p; ++m) {
+        const T d = sDw[m * p + b];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) s[i] += d * F[i][m * p + a];
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) out[i] = s[i] * hx2 * sw[a];
+}
+
 // shared memory: D, Dw, w tables, then nfields element arrays per local element
 // The element order fixed at compile time (KC > 0; KC = 0 keeps the run's order): loops over the
 // K + 1 nodes of an element unroll and slot arithmetic folds.  epb follows the host's choice.
@@ -419,14 +480,18 @@ __global__ void k_chem(Geo<T> G_, Phys<T> q_, const T *__restrict__ phin, const 
     __syncthreads();
     if (act) {
         const T sx = T(2) / hx, sy = T(2) / hy;
-        const T gpx = ddx(sP, sD, G.p, e.a, e.b, sx);
-        const T gpy = ddy(sP, sD, G.p, e.a, e.b, sy);
+        const T *fs[2] = {sP, sQ};   // phi* and Q2, each coefficient loaded once for both
+        T dx[2], dy[2];
+        ddx_n(fs, sD, G.p, e.a, e.b, sx, dx);
+        ddy_n(fs, sD, G.p, e.a, e.b, sy, dy);
+        const T gpx = dx[0];
+        const T gpy = dy[0];
         T adv = star(q.J, uxn[e.g], uxo[e.g]) * gpx + star(q.J, uyn[e.g], uyo[e.g]) * gpy;
         if (uzn) adv += star(q.J, uzn[e.g], uzo[e.g]) * star(q.J, dzphin[e.g], dzphio[e.g]);
         const T phh = hatv(q.J, phin[e.g], phio[e.g]);
         Q1 = (-adv + phh / q.dt) / (q.lam * q.gamma1);
-        sQx[e.t] = ddx(sQ, sD, G.p, e.a, e.b, sx);
-        sQy[e.t] = ddy(sQ, sD, G.p, e.a, e.b, sy);
+        sQx[e.t] = dx[1];
+        sQy[e.t] = dy[1];
     }
     __syncthreads();
     if (!act) return;
@@ -494,23 +559,26 @@ __global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
     if (act) {
         const T sx = T(2) / hx, sy = T(2) / hy;
         const T phi = sphi[e.t];
-        T gphi[3] = {ddx(sphi, sD, G.p, e.a, e.b, sx), ddy(sphi, sD, G.p, e.a, e.b, sy),
-                     d3 ? in.dzphi[e.g] : T(0)};
-        T gW[3] = {ddx(sW, sD, G.p, e.a, e.b, sx), ddy(sW, sD, G.p, e.a, e.b, sy), d3 ? in.dzW[e.g] : T(0)};
+        // x and y derivatives of phi, W, u*_x, u*_y, u*_z (0 in 2D), P*, each coefficient loaded once
+        const T *fs[6] = {sphi, sW, sux, suy, suz, sPs};
+        T dx[6], dy[6];
+        ddx_n(fs, sD, G.p, e.a, e.b, sx, dx);
+        ddy_n(fs, sD, G.p, e.a, e.b, sy, dy);
+        T gphi[3] = {dx[0], dy[0], d3 ? in.dzphi[e.g] : T(0)};
+        T gW[3] = {dx[1], dy[1], d3 ? in.dzW[e.g] : T(0)};
         T gu[3][3];   // gu[c][d] = d u*_c / d x_d
-        gu[0][0] = ddx(sux, sD, G.p, e.a, e.b, sx);
-        gu[0][1] = ddy(sux, sD, G.p, e.a, e.b, sy);
-        gu[1][0] = ddx(suy, sD, G.p, e.a, e.b, sx);
-        gu[1][1] = ddy(suy, sD, G.p, e.a, e.b, sy);
-        gu[2][0] = d3 ? ddx(suz, sD, G.p, e.a, e.b, sx) : T(0);
-        gu[2][1] = d3 ? ddy(suz, sD, G.p, e.a, e.b, sy) : T(0);
+        gu[0][0] = dx[2];
+        gu[0][1] = dy[2];
+        gu[1][0] = dx[3];
+        gu[1][1] = dy[3];
+        gu[2][0] = d3 ? dx[4] : T(0);
+        gu[2][1] = d3 ? dy[4] : T(0);
         if (d3) {
             for (int c = 0; c < 3; ++c) gu[c][2] = star(J, in.dzun[c][e.g], in.dzuo[c][e.g]);
         } else {
             gu[0][2] = gu[1][2] = gu[2][2] = 0;
         }
-        T gP[3] = {ddx(sPs, sD, G.p, e.a, e.b, sx), ddy(sPs, sD, G.p, e.a, e.b, sy),
-                   d3 ? star(J, in.dzPn[e.g], in.dzPo[e.g]) : T(0)};
+        T gP[3] = {dx[5], dy[5], d3 ? star(J, in.dzPn[e.g], in.dzPo[e.g]) : T(0)};
         const T rho = rho_of(q, phi), mu = mu_of(q, phi);
         const T irho = T(1) / rho;
         mr = mu * irho;
@@ -559,7 +627,13 @@ __global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
     const T inu = T(1) / q.nu_m;
     const int p = G.p;
     // pressure: rho0 int G_2D . grad q - rho0 int_wall J_x dq/dx  ;  iB part: -rho0 int G_z q + rho0 int_wall J_z q
-    T ap = q.rho0 * (wdx(sGx, sDw, sw, p, e.a, e.b, hy2) + wdy(sGy, sDw, sw, p, e.a, e.b, hx2));
+    // weak x derivatives of G_x, K_z, K_y and weak y derivatives of G_y, K_z, K_x, each coefficient
+    // loaded once
+    const T *fwx[3] = {sGx, sKz, sKy}, *fwy[3] = {sGy, sKz, sKx};
+    T wx[3], wy[3];
+    wdx_n(fwx, sDw, sw, p, e.a, e.b, hy2, wx);
+    wdy_n(fwy, sDw, sw, p, e.a, e.b, hx2, wy);
+    T ap = q.rho0 * (wx[0] + wy[0]);
     T bp = -q.rho0 * Me * Gv[2];
     if (e.ey == 0 && e.b == 0) {
         // -rho0 int_wall J_x dq/dx with J_x = -(mu/rho) omega_z: 1D weak x-derivative of the face row
@@ -571,9 +645,9 @@ __global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
     out.AP[e.l] = ap;
     if (out.BP) out.BP[e.l] = bp;
     // velocity (without the new pressure): (1/nu_m) int G v - (1/nu_m) int K x grad v - (1/nu_m) int_top L v
-    T ax = inu * (Me * Gv[0] + wdy(sKz, sDw, sw, p, e.a, e.b, hx2));
-    T ay = inu * (Me * Gv[1] - wdx(sKz, sDw, sw, p, e.a, e.b, hy2));
-    T az = inu * (Me * Gv[2] - wdy(sKx, sDw, sw, p, e.a, e.b, hx2) + wdx(sKy, sDw, sw, p, e.a, e.b, hy2));
+    T ax = inu * (Me * Gv[0] + wy[1]);
+    T ay = inu * (Me * Gv[1] - wx[1]);
+    T az = inu * (Me * Gv[2] - wy[2] + wx[2]);
     if (e.ey == G.ey - 1 && e.b == G.K) {
         ax -= inu * hx2 * sw[e.a] * Kf * om[2];      // L_x = (mu/rho - nu_m) omega_z
         az += inu * hx2 * sw[e.a] * Kf * om[0];      // L_z = -(mu/rho - nu_m) omega_x
