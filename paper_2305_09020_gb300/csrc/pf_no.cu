@@ -62,7 +62,8 @@ __global__ void k_dense_fwd(const float *__restrict__ X, const __nv_bfloat16 *__
 // tcgen05.mma kind::f16 (M = 128, N = 64, K = 16) accumulates Wt (hi + lo) in FP32 in tensor memory,
 // the epilogue adds the bias and applies tanh.  Operands are staged by the block's threads in the
 // 128-byte-swizzled K-major layout (K in atoms of 64 BF16; rows of 128 bytes, 16-byte chunks
-// permuted by row mod 8).  The one wait is bounded: on time-out the error word is set.
+// permuted by row mod 8).  The wait is bounded: on time-out the error word is set and the
+// results are not written.
 constexpr int NO_TC_BN = 64;   // samples per CTA
 __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
     // byte offset of BF16 element (row, k) in a K-major, 128B-swizzled tile of `rows` rows
@@ -132,8 +133,11 @@ __global__ void __launch_bounds__(128, 1) k_dense_fwd_tc(const float *__restrict
         }
         pf::mma_commit(pf::smem_u32(mbar));
     }
-    const bool ok = pf::mbar_wait(pf::smem_u32(mbar), 0u, nullptr, 1000000000ull);
-    if (!ok && lane == 0) atomicExch(err, pf::TC_ERR_TIMEOUT);
+    bool ok = pf::mbar_wait(pf::smem_u32(mbar), 0u, nullptr, 1000000000ull);
+    if (!ok) {   // record the time-out, give the MMAs one more bounded wait before the memory goes
+        if (lane == 0) atomicExch(err, pf::TC_ERR_TIMEOUT);
+        pf::mbar_wait(pf::smem_u32(mbar), 0u, nullptr, 1000000000ull);
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         // warp w reads rows (outputs) 32 w .. 32 w + 31, all 64 samples
