@@ -525,7 +525,7 @@ struct MomOut {
 };
 
 template <typename T, int KC = 0>
-__global__ void k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_momentum(Geo<T> G_, Phys<T> q_, MomIn<T> in, MomOut<T> out) {
     if (plane_frozen(G_)) return;
     const Geo<T> G = fixed_order<KC>(G_);
     PF_ELEM_SMEM(T, G, 12)
